@@ -1,0 +1,298 @@
+"""Seeded synthetic access traces: the input side of the race checker.
+
+This module only *builds* inputs.  It holds no race arithmetic: it never
+decides whether two accesses conflict or are ordered.  Both the CUDA checker
+(through its tests and benchmarks) and the CPU oracle consume what it makes.
+
+Trace format (one 16-byte little-endian record per event, array-of-structs):
+
+    offset  size  field    meaning
+    0       4     word     word index inside the checked region (access records)
+    4       4     tid      global thread id = blockIdx * blockDim + threadIdx
+    8       2     wc       warp clock: full-warp __syncwarp() since the last __syncthreads()
+    10      2     bc       block clock: __syncthreads() executed so far in this kernel
+    12      2     kernel   launch ordinal of the traced kernel
+    14      1     op       0 read, 1 write, 2 atomic, 3 __syncthreads, 4 __syncwarp
+    15      1     flags    bit 0: the atomic is an atomic load (informational)
+                           bit 1: __syncwarp with a partial mask (unsupported)
+
+The (bc, wc) pair of an access is the thread-private clock of the paper's
+shadow record (Section III, Fig. 2 / Algorithm 1 inputs `bc`, `wc`).  A sync
+record carries the clocks the thread holds *after* the barrier.  A trace is
+sorted by its wave key (kernel, bc, wc); inside a wave each thread's records
+keep program order.  The bytes at offsets 8..13 read as a little-endian u64,
+masked to 48 bits, are exactly that key.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+RECORD = np.dtype([("word", "<u4"), ("tid", "<u4"), ("wc", "<u2"), ("bc", "<u2"),
+                   ("kernel", "<u2"), ("op", "u1"), ("flags", "u1")])
+assert RECORD.itemsize == 16
+
+OP_R, OP_W, OP_A, OP_SYNCTHREADS, OP_SYNCWARP = 0, 1, 2, 3, 4
+FLAG_ATOMIC_LOAD = 1
+FLAG_PARTIAL_MASK = 2
+
+SEED_BASE = 0x48695261
+
+_OPS = {"R": OP_R, "W": OP_W, "A": OP_A}
+
+
+def seed_for(config: int, trial: int = 0) -> int:
+    """Seed of a workload: fixed base + 1000 * workload number + trial."""
+    return SEED_BASE + config * 1000 + trial
+
+
+def wave_keys(trace: np.ndarray) -> np.ndarray:
+    """(kernel, bc, wc) packed into one integer per record (sort key of a trace)."""
+    return ((trace["kernel"].astype(np.int64) << 32) | (trace["bc"].astype(np.int64) << 16)
+            | trace["wc"].astype(np.int64))
+
+
+def is_sorted(trace: np.ndarray) -> bool:
+    k = wave_keys(trace)
+    return bool(np.all(k[1:] >= k[:-1])) if len(k) > 1 else True
+
+
+# --------------------------------------------------------------------------
+# Hand-written programs (litmus tests, small exhaustive universes)
+# --------------------------------------------------------------------------
+
+def build_trace(kernels, kernel_base: int = 0) -> np.ndarray:
+    """Trace of small hand-written per-thread programs.
+
+    ``kernels`` is a list (one entry per launch) of ``{tid: [event, ...]}``.
+    An event is ``("R"|"W"|"A", word)``, ``("A", word, FLAG_ATOMIC_LOAD)``,
+    ``("ST",)`` for __syncthreads or ``("SW",)`` / ``("SW", FLAG_PARTIAL_MASK)``
+    for __syncwarp.  Each thread's clocks are counted from its own barriers
+    (a thread's clocks restart at every launch).  Records are ordered by wave,
+    then by program step, then by tid: the order a SIMT tracer logging one
+    instruction for all lanes at a time would produce.
+    """
+    rows = []
+    for k, threads in enumerate(kernels):
+        for tid, events in threads.items():
+            bc = wc = 0
+            for step, ev in enumerate(events):
+                kind = ev[0]
+                if kind == "ST":
+                    bc += 1
+                    wc = 0
+                    rows.append((0, tid, wc, bc, kernel_base + k, OP_SYNCTHREADS, 0, step))
+                elif kind == "SW":
+                    wc += 1
+                    fl = ev[1] if len(ev) > 1 else 0
+                    rows.append((0, tid, wc, bc, kernel_base + k, OP_SYNCWARP, fl, step))
+                else:
+                    fl = ev[2] if len(ev) > 2 else 0
+                    rows.append((ev[1], tid, wc, bc, kernel_base + k, _OPS[kind], fl, step))
+    if not rows:
+        return np.zeros(0, RECORD)
+    a = np.array(rows, dtype=np.int64)
+    order = np.lexsort((a[:, 1], a[:, 7], a[:, 2], a[:, 3], a[:, 4]))
+    a = a[order]
+    out = np.zeros(len(a), RECORD)
+    for i, name in enumerate(("word", "tid", "wc", "bc", "kernel", "op", "flags")):
+        out[name] = a[:, i]
+    return out
+
+
+def shuffle_within_waves(trace: np.ndarray, rng: np.random.Generator) -> np.ndarray:
+    """Another valid interleaving: records permuted inside each wave while
+    every thread keeps its own program order."""
+    if len(trace) == 0:
+        return trace.copy()
+    keys = wave_keys(trace)
+    starts = np.flatnonzero(np.r_[True, keys[1:] != keys[:-1]])
+    ends = np.r_[starts[1:], len(trace)]
+    out = trace.copy()
+    for s, e in zip(starts, ends):
+        seg = trace[s:e]
+        perm = rng.permutation(e - s)
+        shuffled = seg[perm]
+        # restore per-thread program order on the positions each thread now holds
+        for tid in np.unique(seg["tid"]):
+            pos = np.flatnonzero(shuffled["tid"] == tid)
+            shuffled[pos] = seg[seg["tid"] == tid]
+        out[s:e] = shuffled
+    return out
+
+
+# --------------------------------------------------------------------------
+# Workload 1: shared-memory tree reduction, one block
+# --------------------------------------------------------------------------
+
+def gen_tree_reduction(seed: int, inject: bool = True, segments: int = 48, block_dim: int = 256,
+                       reps: int = 28, p_unit: float = 0.01, force: bool = True):
+    """One block of ``block_dim`` threads over ``segments`` x ``block_dim`` shared words.
+
+    Epoch k (k = 0..log2(block_dim)-1) has stride s = block_dim/2 >> k; thread t < s
+    reads words t and t+s of every segment and writes word t, ``reps`` times per
+    epoch, with a __syncthreads() between epochs.  Injection: each (segment, epoch)
+    unit draws "double the active bound" (t < 2s, partner index mod block_dim) with
+    probability ``p_unit``; each barrier draws "dropped" with the same probability;
+    when ``force`` and a kind drew nothing, one unit of that kind is forced.
+
+    Returns (trace, info) with info = dict(n_words, block_dim, n_threads, doubled, dropped).
+    """
+    rng = np.random.default_rng(seed)
+    n_epochs = int(np.log2(block_dim))
+    n_words = segments * block_dim
+    doubled = np.zeros((segments, n_epochs), bool)
+    dropped = np.zeros(n_epochs - 1, bool)
+    if inject:
+        doubled = rng.random((segments, n_epochs)) < p_unit
+        dropped = rng.random(n_epochs - 1) < p_unit
+        if force and not doubled.any():
+            doubled[rng.integers(segments), rng.integers(n_epochs)] = True
+        if force and not dropped.any():
+            dropped[rng.integers(n_epochs - 1)] = True
+    # block clock of each epoch after dropped barriers are removed
+    bc_of_epoch = np.zeros(n_epochs, np.int64)
+    for k in range(1, n_epochs):
+        bc_of_epoch[k] = bc_of_epoch[k - 1] + (0 if dropped[k - 1] else 1)
+
+    t_all = np.arange(block_dim)
+    parts = []
+    for k in range(n_epochs):
+        s = (block_dim // 2) >> k
+        bc = bc_of_epoch[k]
+        if k > 0 and not dropped[k - 1]:
+            sync = np.zeros(block_dim, RECORD)
+            sync["tid"] = t_all
+            sync["bc"] = bc
+            sync["op"] = OP_SYNCTHREADS
+            parts.append((np.full(block_dim, bc), np.full(block_dim, k), np.zeros(block_dim), sync))
+        # accesses: grid over (rep, seg, j, t)
+        rep, seg, j, t = np.meshgrid(np.arange(reps), np.arange(segments), np.arange(3), t_all,
+                                     indexing="ij")
+        rep, seg, j, t = rep.ravel(), seg.ravel(), j.ravel(), t.ravel()
+        bound = np.where(doubled[seg, k], 2 * s, s)
+        keep = t < bound
+        rep, seg, j, t = rep[keep], seg[keep], j[keep], t[keep]
+        idx = np.where(j == 1, (t + s) % block_dim, t)
+        rec = np.zeros(len(t), RECORD)
+        rec["word"] = seg * block_dim + idx
+        rec["tid"] = t
+        rec["bc"] = bc
+        rec["op"] = np.where(j == 2, OP_W, OP_R)
+        # SIMT log order inside the epoch: warp, instruction (rep, seg, j), lane
+        step = (rep * segments + seg) * 3 + j + 1
+        parts.append((np.full(len(t), bc), np.full(len(t), k), (t // 32) * (1 << 32) + step * 64 + (t % 32),
+                      rec))
+    bcs = np.concatenate([p[0] for p in parts])
+    eps = np.concatenate([p[1] for p in parts])
+    sub = np.concatenate([p[2] for p in parts]).astype(np.int64)
+    recs = np.concatenate([p[3] for p in parts])
+    order = np.lexsort((sub, eps, bcs))
+    trace = recs[order]
+    info = dict(n_words=n_words, block_dim=block_dim, n_threads=block_dim,
+                doubled=[(int(a), int(b)) for a, b in zip(*np.nonzero(doubled))],
+                dropped=[int(x) for x in np.flatnonzero(dropped)])
+    return trace, info
+
+
+# --------------------------------------------------------------------------
+# Workload 2: global memory, owned tiles + random shared words
+# --------------------------------------------------------------------------
+
+def gen_global_mix(seed: int, inject: bool = True, n_blocks: int = 1024, block_dim: int = 256,
+                   tile_words: int = 65536, epochs: int = 8, subs: int = 4, slots: int = 8,
+                   inject_frac: float = 0.001):
+    """Grid of ``n_blocks`` x ``block_dim`` threads over ``n_blocks * tile_words`` words.
+
+    Every thread makes ``epochs * subs * slots`` accesses: ``slots`` per warp
+    sub-epoch, a __syncwarp() between sub-epochs and a __syncthreads() between
+    epochs.  Each access draws its class: 45% read of a random read-only word,
+    5% atomic on a random atomic-only word (both anywhere in the array), 25%
+    read and 25% write of the block's own tile.  Tile words split by offset:
+    the first quarter is owned (block-strided rows; in epoch e, slot i uses row
+    e*slots+i, column (warp+e) mod warps, lane (lane+sub) mod 32), the next
+    sixteenth is atomic-only, the rest read-only.  Injection retargets
+    ``inject_frac * n_words`` random-class accesses, as writes, to distinct
+    words that a thread of another block touches.
+
+    Returns (trace, info) with info = dict(n_words, block_dim, n_threads, injected).
+    """
+    assert block_dim % 32 == 0
+    nwarp = block_dim // 32
+    ow = tile_words // 4
+    assert epochs * slots * block_dim <= ow, "tile too small for the owned rows"
+    at_lo, at_hi = ow, ow + tile_words // 16
+    ro_lo, ro_hi = at_hi, tile_words
+    n_words = n_blocks * tile_words
+    rng = np.random.default_rng(seed)
+
+    # full grid in wave order: (epoch, sub, block, warp, slot[0 = sync], lane)
+    shape = (epochs, subs, n_blocks, nwarp, slots + 1, 32)
+    n_all = int(np.prod(shape))
+    e = np.arange(epochs, dtype=np.int64).reshape(-1, 1, 1, 1, 1, 1)
+    w = np.arange(subs, dtype=np.int64).reshape(1, -1, 1, 1, 1, 1)
+    b = np.arange(n_blocks, dtype=np.int64).reshape(1, 1, -1, 1, 1, 1)
+    v = np.arange(nwarp, dtype=np.int64).reshape(1, 1, 1, -1, 1, 1)
+    i = np.arange(slots + 1, dtype=np.int64).reshape(1, 1, 1, 1, -1, 1)
+    ln = np.arange(32, dtype=np.int64).reshape(1, 1, 1, 1, 1, -1)
+
+    rec = np.zeros(n_all, RECORD)
+    rec["tid"] = np.broadcast_to(b * block_dim + v * 32 + ln, shape).ravel()
+    rec["bc"] = np.broadcast_to(e, shape).ravel()
+    rec["wc"] = np.broadcast_to(w, shape).ravel()
+    is_sync = np.broadcast_to(i == 0, shape).ravel()
+    sync_op = np.broadcast_to(np.where(w == 0, OP_SYNCTHREADS, OP_SYNCWARP), shape).ravel()
+
+    u = rng.random(n_all, dtype=np.float32)
+    rand_tile = rng.integers(0, n_blocks, n_all, dtype=np.int64)
+    ro_off = rng.integers(ro_lo, ro_hi, n_all, dtype=np.int64)
+    at_off = rng.integers(at_lo, at_hi, n_all, dtype=np.int64)
+    strided = np.broadcast_to(
+        b * tile_words + (e * slots + (i - 1)) * block_dim + ((v + e) % nwarp) * 32 + (ln + w) % 32,
+        shape).ravel()
+
+    cls = np.where(u < 0.45, 0, np.where(u < 0.50, 1, np.where(u < 0.75, 2, 3))).astype(np.int8)
+    word = np.where(cls == 0, rand_tile * tile_words + ro_off,
+                    np.where(cls == 1, rand_tile * tile_words + at_off, strided))
+    del u, rand_tile, ro_off, at_off, strided
+    op = np.where(cls == 0, OP_R, np.where(cls == 1, OP_A, np.where(cls == 2, OP_R, OP_W)))
+    rec["word"] = np.where(is_sync, 0, word)
+    rec["op"] = np.where(is_sync, sync_op, op)
+    del word, op
+    cls = np.where(is_sync, -1, cls)
+
+    keep = ~(is_sync & (rec["bc"] == 0) & (rec["wc"] == 0))
+    rec = rec[keep]
+    cls = cls[keep]
+
+    injected = np.zeros(0, np.int64)
+    if inject:
+        n_inj = int(inject_frac * n_words)
+        random_idx = np.flatnonzero((cls == 0) | (cls == 1))
+        source_pool = np.flatnonzero((cls == 0) | (cls >= 2))
+        carriers = rng.choice(random_idx, size=n_inj, replace=False)
+        carrier_mask = np.zeros(len(rec), bool)
+        carrier_mask[carriers] = True
+        source_pool = source_pool[~carrier_mask[source_pool]]
+        cblock = rec["tid"][carriers] // block_dim
+        targets = np.full(n_inj, -1, np.int64)
+        taken = set()
+        todo = np.arange(n_inj)
+        while len(todo):
+            src = rng.choice(source_pool, size=len(todo))
+            cand = rec["word"][src].astype(np.int64)
+            ok = (rec["tid"][src] // block_dim) != cblock[todo]
+            nxt = []
+            for j, c, good in zip(todo, cand, ok):
+                if good and c not in taken:
+                    taken.add(int(c))
+                    targets[j] = c
+                else:
+                    nxt.append(j)
+            todo = np.array(nxt, dtype=np.int64)
+        rec["word"][carriers] = targets
+        rec["op"][carriers] = OP_W
+        rec["flags"][carriers] = 0
+        injected = np.sort(targets)
+    info = dict(n_words=n_words, block_dim=block_dim, n_threads=n_blocks * block_dim,
+                injected=injected)
+    return rec, info
