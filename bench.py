@@ -1,0 +1,272 @@
+"""Benchmark: checked accesses per second on the global-memory workload.
+
+Workload (one step = one full check of one trace): a grid of 1024 blocks x 256
+threads over 2^26 shadowed words, 256 accesses per thread (70% read, 25% write,
+5% atomicAdd; half block-strided in the block's own tile, half uniform-random),
+__syncwarp every 8 and __syncthreads every 32 accesses, 0.1% of the words made
+racy across blocks: 67,108,864 accesses + 8,126,464 barrier records
+(75,235,328 records, 1.20 GB).  Synthetic, seeded; inputs (1.2 GB trace,
+512 MB shadow) are larger than L2, so no flush is needed between steps.
+
+Each timed step checks the trace as the next kernel launch of the same region
+(kernel_base = step), so the shadow's kernel tags make older values read as
+INIT and every eighth step includes the group clear of the whole shadow.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed.run: every rank checks its own replica of
+the workload (the checker shards by independent trace, no collective on the
+data path); value = all ranks' accesses / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "checked accesses/sec vs HBM roofline"
+UNIT = "accesses/s"
+WORKLOAD = "global-mix: 1024x256 threads, 2^26 words, 67.1M accesses + 8.1M barrier records"
+ALG_BYTES_PER_ACCESS = 32   # 16 B record + 8 B shadow read + 8 B shadow write
+ALG_BYTES_PER_SYNC = 16     # a barrier record is streamed, not an access
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(gpu_index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload():
+    from paper_2401_04701_gb300 import tracegen as tg
+    trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True)
+    n_acc = int(np.count_nonzero(trace["op"] <= tg.OP_A))
+    n_sync = len(trace) - n_acc
+    return trace, info, n_acc, n_sync
+
+
+def cpu_oracle_rate(trace, info, n_acc, max_records=None):
+    """Serial FSM oracle (C, one core) over a sample of the trace: (accesses/s, seconds, sample)."""
+    from oracle import oracle
+    sample = trace if max_records is None else trace[:max_records]
+    acc = int(np.count_nonzero(sample["op"] <= 2)) if max_records is not None else n_acc
+    t0 = time.perf_counter()
+    oracle.serial_fsm(sample, info["block_dim"], info["n_words"])
+    dt = time.perf_counter() - t0
+    return acc / dt, dt, acc
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    trace, info, n_acc, n_sync = make_workload()
+    # bounded sample: the first block epoch (bc == 0) of the same trace
+    cut = int(np.searchsorted((trace["bc"] > 0).view(np.uint8), 1))
+    for _ in range(args.warmup):
+        cpu_oracle_rate(trace, info, n_acc, max_records=cut)
+    tot_acc, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        _, dt, acc = cpu_oracle_rate(trace, info, n_acc, max_records=cut)
+        tot_acc += acc
+        tot_t += dt
+    value = tot_acc / tot_t
+    sample = "first block epoch of the workload (%d records, %d accesses), serial FSM oracle" % (cut, tot_acc // args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bc==0 epoch"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    from paper_2401_04701_gb300 import hirace
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    hirace.load_library()
+
+    trace, info, n_acc, n_sync = make_workload()
+    host = torch.from_numpy(trace.view(np.uint8)).pin_memory()
+    d_trace = host.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ring = 1 << 22
+    ck = hirace.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])], report_capacity=ring)
+
+    # correctness gate: one check vs the injected set
+    ck.check_trace(0, d_trace)
+    races, status, n_total, _ = ck.report(0)
+    if status != hirace.HR_OK or n_total != len(info["injected"]):
+        raise SystemExit("bench workload check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
+    ck.reset(0)
+    torch.cuda.synchronize()
+
+    kb = 0
+    for _ in range(args.warmup):
+        ck.check_trace(0, d_trace, kernel_base=kb)
+        kb += 1
+    torch.cuda.synchronize()
+    ck.profile(True)
+    ck.profile_read()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local_rank) if rank == 0 else None
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        ck.check_trace(0, d_trace, kernel_base=kb)
+        kb += 1
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    ms = start.elapsed_time(stop)
+    prof = ck.profile_read()
+    ck.profile(False)
+    _, status, _, _ = ck.report(0)
+    if status != hirace.HR_OK:
+        raise SystemExit("timed steps ended with %s" % hirace.STATUS[status])
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end through the C-ABI from pinned host memory: H2D of the trace,
+    # reset, check, D2H of the race records
+    e2e_steps = max(1, min(args.steps, 10))
+    d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        d_trace.copy_(host, non_blocking=True)
+        ck.reset(0)
+        ck.check_trace(0, d_trace)
+        races, status, n_total, _ = ck.report(0)
+        d2h += races.nbytes + 64
+    e2e_s = time.perf_counter() - t0
+    e2e_rate = world * n_acc * e2e_steps / e2e_s
+
+    if rank != 0:
+        ck.close()
+        return
+    value = world * n_acc * args.steps / (ms / 1e3)
+    p_hbm, peak_kind = peaks()
+    alg_bytes = n_acc * ALG_BYTES_PER_ACCESS + n_sync * ALG_BYTES_PER_SYNC
+    check_ms = prof["check_ms"] / max(1, prof["calls"])
+    achieved = alg_bytes / (check_ms / 1e3) / 1e9
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, dt, acc = cpu_oracle_rate(trace, info, n_acc)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "whole workload once (%d accesses, %.1f s), serial FSM oracle in C" % (acc, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_words": info["n_words"], "records": len(trace), "accesses": n_acc,
+                   "shadow_bytes_per_word": 8, "racy_words": int(len(info["injected"])),
+                   "l2": "inputs larger than L2 (1.2 GB trace, 512 MB shadow), no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
+                     "frac": achieved / p_hbm, "traffic": None, "kernel": "hr_check_kernel<true>",
+                     "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
+                     "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
+        "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
+                "d2h_bytes_per_step": int(d2h // e2e_steps)},
+        "gpu_launches": int(prof["launches"]),
+        "clocks": clk,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    ck.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    run_gpu(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * hirace.h - C-ABI of the GB300 race checker (HiRace, arXiv 2401.04701).
+ *
+ * The checker folds the access history of every monitored word into a
+ * constant-size 8-byte shadow value with a parallel finite-state machine
+ * (Sec. III; Algorithm 1 "UpdateShadow"; 8 bytes per word by default,
+ * Sec. IV-B) and reports the words on which two accesses race (Sec. II-A:
+ * different threads, at least one write, not ordered by happens-before;
+ * Sec. II-B: __syncthreads orders a block, __syncwarp a warp, nothing orders
+ * two blocks of one kernel, kernel end orders everything).
+ *
+ * Every entry point is extern "C", takes plain pointers and sizes, returns an
+ * hr_status and never throws.  Device pointers are CUDA global-memory
+ * addresses of the current device; streams are cudaStream_t values (NULL is
+ * the legacy default stream).  All work is issued asynchronously on the given
+ * stream unless a call says otherwise.
+ */
+#ifndef HIRACE_H
+#define HIRACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* hr_stream_t; /* same type as cudaStream_t */
+typedef struct hr_ctx hr_ctx;            /* opaque checker context */
+
+typedef enum hr_status {
+    HR_OK = 0,
+    HR_ERR_INVALID = 1,        /* bad argument or region descriptor */
+    HR_ERR_OOM = 2,            /* device or host allocation failed */
+    HR_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+    HR_ERR_ORDER = 4,          /* trace not sorted by (kernel, bc, wc), or older than the region's last record */
+    HR_ERR_RANGE = 5,          /* word index >= n_words */
+    HR_ERR_CLOCK_OVERFLOW = 6, /* a clock does not fit the shadow packing (Sec. III-A footnote) */
+    HR_ERR_CONTENTION = 7,     /* the CAS retry cap was reached on some word */
+    HR_ERR_TIMEOUT = 8,        /* a bounded device-side wait expired */
+    HR_ERR_UNSUPPORTED = 9,    /* partial-mask __syncwarp or an unknown op code */
+    HR_ERR_CAPACITY = 10,      /* more waves in one call than the wave table holds */
+    HR_ERR_NOT_READY = 11      /* the region has work in flight on another stream */
+} hr_status;
+
+/* hr_report flag bits */
+#define HR_FLAG_TRUNCATED 1u /* more races than the report ring holds; n_total stays exact */
+
+/* memory space of a region (informational: the shadow always lives in HBM) */
+#define HR_SPACE_GLOBAL 0u
+#define HR_SPACE_SHARED 1u
+
+/* hr_sync scopes */
+#define HR_SYNC_KERNEL 0u
+
+/* access operations (Algorithm 1 input `access`: read / write / atomic) and
+ * barrier records (Sec. II-B) */
+typedef enum hr_op {
+    HR_R = 0,
+    HR_W = 1,
+    HR_A = 2,
+    HR_SYNCTHREADS = 3,
+    HR_SYNCWARP = 4
+} hr_op;
+
+#define HR_RECFLAG_ATOMIC_LOAD 1u  /* informational */
+#define HR_RECFLAG_PARTIAL_MASK 2u /* __syncwarp with a partial mask: unsupported (Sec. VI future work) */
+
+/*
+ * One trace record, 16 bytes, little endian.  `tid` is the global thread id
+ * blockIdx*blockDim+threadIdx (Algorithm 1 input "Global thread ID"); `bc`
+ * and `wc` are the thread-private block-scope and warp-scope scalar clocks
+ * (Algorithm 1 inputs `bc`, `wc`; Sec. III-A Scenario 2): bc counts the
+ * __syncthreads the thread has executed in this kernel, wc the full-warp
+ * __syncwarp since its last __syncthreads.  A barrier record carries the
+ * clocks the thread holds after the barrier.  Bytes 8..13 read as a
+ * little-endian u64 masked to 48 bits form the wave key (kernel, bc, wc).
+ */
+typedef struct hr_record {
+    uint32_t word;   /* word index inside the region (ignored for barrier records) */
+    uint32_t tid;
+    uint16_t wc;
+    uint16_t bc;
+    uint16_t kernel; /* launch ordinal of the traced kernel */
+    uint8_t op;      /* hr_op */
+    uint8_t flags;   /* HR_RECFLAG_* */
+} hr_record;
+
+/*
+ * One race report, 16 bytes: the first racy pair on `word` inside `kernel`
+ * was completed by an access of thread `tid` doing `op` in block epoch
+ * `epoch` (its bc).  `prior` is the FSM state the word held just before
+ * (hr_fsm_state_name).  Races are reported once per (word, kernel) ("report
+ * races on unique memory addresses", Sec. V-B).
+ */
+typedef struct hr_race {
+    uint32_t word;
+    uint32_t tid;
+    uint16_t kernel;
+    uint16_t epoch;
+    uint16_t region;
+    uint8_t op;
+    uint8_t prior;
+} hr_race;
+
+/* Geometry of one monitored region: its words and the traced launch shape. */
+typedef struct hr_region_desc {
+    uint64_t n_words;         /* monitored words, >= 1 */
+    uint32_t block_dim;       /* threads per block of the traced kernels, >= 1 */
+    uint32_t warp_size;       /* 32 on NVIDIA GPUs; 1..32 for small test universes */
+    uint32_t space;           /* HR_SPACE_GLOBAL or HR_SPACE_SHARED (informational) */
+    uint32_t reserved;        /* must be 0 */
+    uint64_t report_capacity; /* race records kept for this region; 0 = the hr_init default */
+} hr_region_desc;
+
+/*
+ * hr_init - create a checker context with one shadow store per region
+ * (Sec. III-A: "we create a shadow[k] entry for each array element data[k]";
+ * 8 bytes per word, Sec. IV-B).  Every shadow word starts in INIT.
+ *   out              receives the context (host pointer; NULL on failure)
+ *   regions          n_regions host descriptors
+ *   report_capacity  default race records per region (>= 1)
+ *   stream           stream for the initial clears
+ * The context owns all device memory it allocates (shadow: 8*n_words bytes
+ * per region; report ring: 16*report_capacity bytes per region; a wave table
+ * and control block).  Errors: HR_ERR_INVALID, HR_ERR_OOM, HR_ERR_CUDA.
+ */
+hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
+                  uint64_t report_capacity, hr_stream_t stream);
+
+/*
+ * hr_check_trace - apply a device-resident trace to one region (Algorithm 1
+ * for every access record, in an order consistent with happens-before).
+ *   d_trace  n records in device memory, caller-owned, alive until `stream`
+ *            passes this call; sorted by wave key (kernel, bc, wc), each
+ *            thread's records in program order, kernels not older than the
+ *            region's last processed record
+ * Asynchronous.  Violations found on the device set the region's sticky
+ * error (HR_ERR_ORDER, HR_ERR_RANGE, HR_ERR_CLOCK_OVERFLOW,
+ * HR_ERR_CONTENTION, HR_ERR_UNSUPPORTED, HR_ERR_CAPACITY, HR_ERR_TIMEOUT);
+ * checking of that region stops after the races found so far are reported
+ * (Sec. III-A footnote), and hr_report returns the error.  Returns
+ * HR_ERR_INVALID for a bad region or NULL trace with n > 0.
+ */
+hr_status hr_check_trace(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                         hr_stream_t stream);
+
+/*
+ * hr_check_trace_kbase - hr_check_trace with `kernel_base` (0..65535) added to
+ * every record's kernel ordinal: one recorded trace can be checked again as a
+ * later launch without clearing the region (kernel end orders everything,
+ * Sec. II-B, so shadow values of older launches read as INIT).  The rebased
+ * ordinals must fit in 16 bits.  Same ownership and errors as hr_check_trace.
+ */
+hr_status hr_check_trace_kbase(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                               uint32_t kernel_base, hr_stream_t stream);
+
+/*
+ * hr_check_trace_plain - the same check without warp aggregation: every lane
+ * applies its own record with its own CAS loop.  Same arguments, ownership
+ * and errors as hr_check_trace; kept as the one-record-per-update baseline.
+ */
+hr_status hr_check_trace_plain(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                               hr_stream_t stream);
+
+/*
+ * hr_sync - kernel end for a region (Sec. II-B: the end of a kernel orders
+ * every access of that kernel before every access of the next one).  Only
+ * HR_SYNC_KERNEL exists: block and warp barriers arrive as trace records or
+ * through the device header.  Later trace records must carry a larger kernel
+ * ordinal; the next device view uses the next kernel ordinal.  Asynchronous.
+ */
+hr_status hr_sync(hr_ctx* ctx, uint32_t region, uint32_t scope, hr_stream_t stream);
+
+/*
+ * hr_report - wait for the region's outstanding work, then copy its race
+ * records to host memory.
+ *   host_out  host array of cap records (may be NULL when cap == 0)
+ *   n_total   receives the number of races found (may exceed cap)
+ *   flags     receives HR_FLAG_* bits (may be NULL)
+ * Records are in the order the device appended them (sort them for a set
+ * comparison).  Returns the region's sticky error, HR_OK if none.
+ */
+hr_status hr_report(hr_ctx* ctx, uint32_t region, hr_race* host_out, uint64_t cap, uint64_t* n_total,
+                    uint32_t* flags);
+
+/* Counters of one region since init/reset: accesses applied, CAS attempts,
+ * CAS retries, lanes merged by warp aggregation.  Synchronises like hr_report. */
+hr_status hr_counters(hr_ctx* ctx, uint32_t region, uint64_t out[4]);
+
+/* hr_reset - every shadow word of the region back to INIT, reports, counters
+ * and error cleared, kernel ordinal back to 0.  Asynchronous. */
+hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream);
+
+/* hr_destroy - synchronise and free everything the context owns. */
+hr_status hr_destroy(hr_ctx* ctx);
+
+/*
+ * Profiling (no paper counterpart; measurement support).  With profiling on,
+ * every check call records CUDA events on its stream around the wave
+ * pre-pass and around the FSM kernel.  hr_profile_read waits for those
+ * events and returns the summed milliseconds, the number of profiled calls
+ * and of library kernel launches since the previous read.  Host pointers may
+ * be NULL.
+ */
+hr_status hr_profile_enable(hr_ctx* ctx, int on);
+hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uint64_t* calls, uint64_t* launches);
+
+/* Static text for a status code. */
+const char* hr_status_str(hr_status s);
+
+/*
+ * The FSM as a flat table (Sec. IV-B: "encoded as a flat array indexed by a
+ * concatenation of oState and the transition labels"): entry
+ * (oState << 6) | (access << 4) | (tRel << 2) | sRel gives the next state in
+ * bits 0..4 and its scope level in bits 5..7 (0xFF marks unused labels).
+ * access: 0 R, 1 W, 2 A.  tRel: 0 same thread, 1 same warp, 2 same block,
+ * 3 other block.  sRel: 0 unsynchronised, 1 warp barrier between, 2 block
+ * barrier between.  Copies 2048 bytes to out; *n_states gets the number of
+ * reachable states.  Host only; needs no GPU.
+ */
+hr_status hr_fsm_table(uint8_t* out, uint32_t* n_states);
+
+/* Name of an FSM state id (e.g. "INIT", "RACE", "T[R|R|R]"); "?" if unused. */
+const char* hr_fsm_state_name(uint32_t state);
+
+/* Library version string. */
+const char* hr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIRACE_H */

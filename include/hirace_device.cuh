@@ -1,0 +1,260 @@
+/*
+ * hirace_device.cuh - device side of the race checker.
+ *
+ * 1. The shadow value and the FSM step (Sec. IV-B, Algorithm 1
+ *    UpdateShadow): unpack <oState, oTid, oBC, oWC>, compareTids -> tRel,
+ *    checkSync -> sRel, one flat-table lookup, pack <nState, tid, bc, wc>,
+ *    atomicCAS until it sticks.  The library's trace kernels use the same
+ *    code through hr_fsm_step().
+ * 2. Source-level instrumentation for hand-written kernels (Sec. IV-A: the
+ *    wrapper "overrides relevant operators ... atomic functions and
+ *    synchronization primitives"): call hr_access() next to every monitored
+ *    load, store or atomic, and use hr_syncthreads() / hr_syncwarp() in place
+ *    of __syncthreads() / __syncwarp() so the thread-private clocks advance
+ *    at the barrier (Sec. III-A Scenario 2).
+ *
+ * Shadow value, 8 bytes per monitored word (Sec. IV-B default):
+ *     bits 63..59  FSM state (5 bits; 0 = INIT, 31 = RACE)
+ *     bits 58..56  kernel tag (kernel ordinal mod 8; a stale tag reads as INIT)
+ *     bits 55..40  bc of the last accessor (16 bits)
+ *     bits 39..32  wc of the last accessor (8 bits)
+ *     bits 31..0   global tid of the last accessor
+ * Only the fields a state needs are kept; the others are zero, so an access
+ * that leaves the summarised history unchanged produces the identical value
+ * and needs no atomic at all:
+ *     thread scope: tid, bc, wc      warp scope: warp's first tid, bc, wc
+ *     block scope:  block's first tid, bc      grid scope and RACE: nothing
+ */
+#ifndef HIRACE_DEVICE_CUH
+#define HIRACE_DEVICE_CUH
+
+#include <stdint.h>
+
+#include "hirace.h"
+
+#define HR_SH_STATE_SHIFT 59
+#define HR_SH_KTAG_SHIFT 56
+#define HR_SH_BC_SHIFT 40
+#define HR_SH_WC_SHIFT 32
+#define HR_WC_MAX 255u
+#define HR_BC_MAX 65535u
+#define HR_STATE_INIT 0u
+#define HR_STATE_RACE 31u
+#define HR_CAS_RETRY_CAP 4096
+
+/* scope level of a state (bits 5..7 of a table entry) */
+#define HR_LVL_INIT 0u
+#define HR_LVL_THREAD 1u
+#define HR_LVL_WARP 2u
+#define HR_LVL_BLOCK 3u
+#define HR_LVL_GRID 4u
+#define HR_LVL_RACE 5u
+
+/* thread relation (compareTids) and sync status (checkSync) labels */
+#define HR_TREL_SAME 0u
+#define HR_TREL_WARP 1u
+#define HR_TREL_BLOCK 2u
+#define HR_TREL_GRID 3u
+#define HR_SREL_UNSYNC 0u
+#define HR_SREL_WARP 1u
+#define HR_SREL_BLOCK 2u
+
+/* Thread geometry of a region: divisions by block_dim and warp_size use a
+ * precomputed 64-bit reciprocal (Lemire, Kaser & Kurz 2019, "Faster remainder
+ * by direct computation": q = hi64(n * (floor((2^64-1)/d) + 1)) is exact for
+ * every 32-bit n); magic 0 stands for d == 1. */
+typedef struct hr_geom {
+    uint32_t block_dim;
+    uint32_t warp_size;
+    uint64_t bd_magic;
+    uint64_t ws_magic;
+} hr_geom;
+
+/* Everything an instrumented kernel needs for one region; pass by value. */
+typedef struct hr_view {
+    unsigned long long* shadow;     /* n_words shadow values */
+    hr_race* ring;                  /* ring_cap race records */
+    unsigned long long* n_races;    /* race counter (may exceed ring_cap) */
+    unsigned int* error;            /* sticky error word (first error wins) */
+    unsigned int* flags;            /* HR_FLAG_* bits */
+    const unsigned char* table;     /* 2048-byte FSM table */
+    unsigned long long n_words;
+    unsigned long long ring_cap;
+    hr_geom geom;
+    unsigned int kernel;            /* kernel ordinal of the launch being checked */
+    unsigned int region;
+} hr_view;
+
+/* Thread-private clocks of an instrumented thread. */
+typedef struct hr_clock {
+    uint32_t tid;
+    uint32_t bc;
+    uint32_t wc;
+} hr_clock;
+
+#ifdef __CUDACC__
+
+static __device__ __forceinline__ uint32_t hr_fastdiv(uint32_t n, uint64_t magic)
+{
+    return magic ? (uint32_t)__umul64hi(magic, (uint64_t)n) : n;
+}
+
+/* One FSM transition: fold access (tid, op, bc, wc) of kernel tag `ktag` into
+ * the raw shadow value `o`.  `table` is the 2048-entry flat table (shared or
+ * global memory).  Returns the new packed value; *raced is set to 1 + the old
+ * state when this access moves the word into RACE, else left alone. */
+static __device__ __forceinline__ uint64_t hr_fsm_step(uint64_t o, uint32_t tid, uint32_t op, uint32_t bc,
+                                                       uint32_t wc, uint32_t ktag, const hr_geom& g,
+                                                       const unsigned char* table, uint32_t* raced)
+{
+    uint32_t os = (uint32_t)(o >> HR_SH_STATE_SHIFT);
+    if (os != HR_STATE_INIT && (uint32_t)((o >> HR_SH_KTAG_SHIFT) & 7u) != ktag) os = HR_STATE_INIT;
+    const uint32_t blk = hr_fastdiv(tid, g.bd_magic);
+    const uint32_t loc = tid - blk * g.block_dim;
+    const uint32_t warp = hr_fastdiv(loc, g.ws_magic);
+    const uint32_t lane = loc - warp * g.warp_size;
+    const uint32_t otid = (uint32_t)o;
+    uint32_t trel;
+    if (otid == tid) {
+        trel = HR_TREL_SAME;
+    } else {
+        const uint32_t oblk = hr_fastdiv(otid, g.bd_magic);
+        if (oblk != blk) {
+            trel = HR_TREL_GRID;
+        } else {
+            const uint32_t owarp = hr_fastdiv(otid - oblk * g.block_dim, g.ws_magic);
+            trel = owarp == warp ? HR_TREL_WARP : HR_TREL_BLOCK;
+        }
+    }
+    const uint32_t obc = (uint32_t)(o >> HR_SH_BC_SHIFT) & 0xFFFFu;
+    const uint32_t owc = (uint32_t)(o >> HR_SH_WC_SHIFT) & 0xFFu;
+    const uint32_t srel = bc != obc ? HR_SREL_BLOCK : (wc != owc ? HR_SREL_WARP : HR_SREL_UNSYNC);
+    const uint32_t e = table[(os << 6) | (op << 4) | (trel << 2) | srel];
+    const uint32_t ns = e & 31u;
+    const uint32_t lvl = e >> 5;
+    uint64_t n = ((uint64_t)ns << HR_SH_STATE_SHIFT) | ((uint64_t)ktag << HR_SH_KTAG_SHIFT);
+    if (lvl == HR_LVL_THREAD)
+        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT) | tid;
+    else if (lvl == HR_LVL_WARP)
+        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT) | (tid - lane);
+    else if (lvl == HR_LVL_BLOCK)
+        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | (tid - loc);
+    if (ns == HR_STATE_RACE && os != HR_STATE_RACE) *raced = 1u + os;
+    return n;
+}
+
+static __device__ __forceinline__ uint64_t hr_ld_relaxed(const unsigned long long* p)
+{
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+static __device__ __forceinline__ void hr_set_error(unsigned int* err, unsigned int code)
+{
+    atomicCAS(err, 0u, code);
+}
+
+/* Append one race record; the counter keeps counting past the capacity. */
+static __device__ __forceinline__ void hr_append_race(hr_race* ring, unsigned long long ring_cap,
+                                                      unsigned long long* n_races, unsigned int* flags,
+                                                      uint32_t word, uint32_t tid, uint32_t kernel,
+                                                      uint32_t epoch, uint32_t region, uint32_t op,
+                                                      uint32_t prior)
+{
+    const unsigned long long slot = atomicAdd(n_races, 1ull);
+    if (slot < ring_cap) {
+        hr_race r;
+        r.word = word;
+        r.tid = tid;
+        r.kernel = (uint16_t)kernel;
+        r.epoch = (uint16_t)epoch;
+        r.region = (uint16_t)region;
+        r.op = (uint8_t)op;
+        r.prior = (uint8_t)prior;
+        ring[slot] = r;
+    } else {
+        atomicOr(flags, HR_FLAG_TRUNCATED);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Hand instrumentation
+ * ------------------------------------------------------------------------- */
+
+/* Clocks of the calling thread at kernel start (1-D or flattened launch). */
+static __device__ __forceinline__ hr_clock hr_clock_init(void)
+{
+    hr_clock c;
+    const uint32_t tpb = blockDim.x * blockDim.y * blockDim.z;
+    const uint32_t b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const uint32_t t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    c.tid = b * tpb + t;
+    c.bc = 0;
+    c.wc = 0;
+    return c;
+}
+
+/* __syncthreads() plus the block-clock advance (bc++, wc = 0). */
+static __device__ __forceinline__ void hr_syncthreads(hr_clock& c)
+{
+    __syncthreads();
+    c.bc += 1;
+    c.wc = 0;
+}
+
+/* full-mask __syncwarp() plus the warp-clock advance (wc++). */
+static __device__ __forceinline__ void hr_syncwarp(hr_clock& c)
+{
+    __syncwarp();
+    c.wc += 1;
+}
+
+/* Record one access (op = HR_R, HR_W or HR_A) to monitored word `word`.
+ * Call it right next to the real access; the two need not be atomic together
+ * (Sec. III-A).  Errors go to the view's sticky error word; the first one
+ * wins and hr_report returns it. */
+static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long long word, uint32_t op,
+                                                 const hr_clock& c)
+{
+    if (word >= v.n_words || op > HR_A) {
+        hr_set_error(v.error, word >= v.n_words ? HR_ERR_RANGE : HR_ERR_UNSUPPORTED);
+        return;
+    }
+    if (c.bc > HR_BC_MAX || c.wc > HR_WC_MAX) {
+        hr_set_error(v.error, HR_ERR_CLOCK_OVERFLOW);
+        return;
+    }
+    unsigned long long* p = v.shadow + word;
+    const uint32_t ktag = v.kernel & 7u;
+    uint64_t o = hr_ld_relaxed(p);
+    for (int it = 0; it < HR_CAS_RETRY_CAP; ++it) {
+        uint32_t raced = 0;
+        const uint64_t n = hr_fsm_step(o, c.tid, op, c.bc, c.wc, ktag, v.geom, v.table, &raced);
+        if (n == o) return;
+        const uint64_t prev = atomicCAS(p, (unsigned long long)o, (unsigned long long)n);
+        if (prev == o) {
+            if (raced)
+                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)word, c.tid, v.kernel, c.bc,
+                               v.region, op, raced - 1u);
+            return;
+        }
+        o = prev;
+    }
+    hr_set_error(v.error, HR_ERR_CONTENTION);
+}
+
+#endif /* __CUDACC__ */
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+/* Host: a by-value view of one region for instrumented kernels.  The view is
+ * valid while the context lives; its kernel ordinal is the region's current
+ * one (advanced by hr_sync).  Returns HR_ERR_INVALID for a bad region. */
+hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out);
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HIRACE_DEVICE_CUH */

@@ -1,0 +1,361 @@
+// hr_api.cu - the C-ABI entry points declared in include/hirace.h.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "hr_internal.h"
+
+namespace {
+
+struct RegionHost {
+    hr_region_desc desc{};
+    hr_region_dev* d = nullptr;           // element of the context's device region array
+    unsigned long long* shadow = nullptr;
+    hr_race* ring = nullptr;
+    unsigned long long ring_cap = 0;
+    void* work_mem = nullptr;
+    hr_work work{};
+    unsigned kernel = 0;                  // kernel ordinal seen by device views
+    cudaEvent_t done = nullptr;           // recorded after every call on the region
+};
+
+uint64_t magic_for(uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; }
+
+hr_status cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return HR_OK;
+    if (e == cudaErrorMemoryAllocation) return HR_ERR_OOM;
+    return HR_ERR_CUDA;
+}
+
+unsigned max_waves_setting()
+{
+    const char* s = getenv("HR_MAX_WAVES");
+    long v = s ? strtol(s, nullptr, 10) : 0;
+    if (v < 1 || v > (1l << 24)) v = 1l << 16;
+    return (unsigned)v;
+}
+
+}  // namespace
+
+struct ProfiledCall {
+    cudaEvent_t begin, mid, end;  // before the pre-pass, before the checker, after it
+    unsigned launches;
+};
+
+struct hr_ctx {
+    int device = 0;
+    std::vector<RegionHost> regions;
+    hr_region_dev* d_regions = nullptr;
+    unsigned char* d_table = nullptr;
+    bool profile = false;
+    std::vector<ProfiledCall> calls;   // profiled calls not read yet
+    std::vector<ProfiledCall> spare;   // event triples to reuse
+};
+
+static ProfiledCall take_events(hr_ctx* c)
+{
+    if (!c->spare.empty()) {
+        ProfiledCall p = c->spare.back();
+        c->spare.pop_back();
+        return p;
+    }
+    ProfiledCall p{};
+    cudaEventCreate(&p.begin);
+    cudaEventCreate(&p.mid);
+    cudaEventCreate(&p.end);
+    return p;
+}
+
+static void free_ctx(hr_ctx* c)
+{
+    if (!c) return;
+    for (auto& r : c->regions) {
+        if (r.done) cudaEventDestroy(r.done);
+        cudaFree(r.shadow);
+        cudaFree(r.ring);
+        cudaFree(r.work_mem);
+    }
+    for (auto* v : {&c->calls, &c->spare})
+        for (auto& p : *v) {
+            cudaEventDestroy(p.begin);
+            cudaEventDestroy(p.mid);
+            cudaEventDestroy(p.end);
+        }
+    cudaFree(c->d_regions);
+    cudaFree(c->d_table);
+    delete c;
+}
+
+static bool valid_region(hr_ctx* ctx, uint32_t region) { return ctx && region < ctx->regions.size(); }
+
+extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
+                             uint64_t report_capacity, hr_stream_t stream)
+{
+    if (!out) return HR_ERR_INVALID;
+    *out = nullptr;
+    if (!regions || n_regions == 0 || n_regions > 65535 || report_capacity == 0) return HR_ERR_INVALID;
+    for (uint32_t i = 0; i < n_regions; ++i) {
+        const hr_region_desc& d = regions[i];
+        if (d.n_words == 0 || d.n_words > (1ull << 32) || d.block_dim == 0 || d.warp_size == 0 ||
+            d.warp_size > 32 || d.reserved != 0 || d.space > HR_SPACE_SHARED)
+            return HR_ERR_INVALID;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    hr_ctx* c = new (std::nothrow) hr_ctx;
+    if (!c) return HR_ERR_OOM;
+    cudaGetDevice(&c->device);
+    c->regions.resize(n_regions);
+    hr_status st = HR_OK;
+    uint8_t table[2048];
+    hr_fsm_table(table, nullptr);
+    cudaError_t e = cudaMalloc(&c->d_table, sizeof table);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_table, table, sizeof table, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_regions, sizeof(hr_region_dev) * n_regions);
+    const unsigned max_waves = max_waves_setting();
+    std::vector<hr_region_dev> hdev(n_regions);
+    for (uint32_t i = 0; i < n_regions && e == cudaSuccess; ++i) {
+        RegionHost& r = c->regions[i];
+        r.desc = regions[i];
+        r.ring_cap = regions[i].report_capacity ? regions[i].report_capacity : report_capacity;
+        r.d = c->d_regions + i;
+        e = cudaMalloc(&r.shadow, r.desc.n_words * sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
+        // scratch of one trace check: interval counts, wave table, stages, control block
+        const size_t b_counts = HR_MAX_INTERVALS * sizeof(unsigned);
+        const size_t b_start = (size_t)(max_waves + 1) * sizeof(unsigned long long);
+        const size_t b_key = (size_t)max_waves * sizeof(unsigned long long);
+        const size_t b_stages = (size_t)(2 * max_waves + 1) * sizeof(hr_stage);
+        const size_t total = b_counts + b_start + b_key + b_stages + sizeof(hr_ctl) + 256;
+        if (e == cudaSuccess) e = cudaMalloc(&r.work_mem, total);
+        if (e == cudaSuccess) {
+            char* p = (char*)r.work_mem;
+            r.work.counts = (unsigned*)p;
+            p += b_counts;
+            r.work.wave_start = (unsigned long long*)p;
+            p += b_start;
+            r.work.wave_key = (unsigned long long*)p;
+            p += b_key;
+            r.work.stages = (hr_stage*)p;
+            p += b_stages;
+            r.work.ctl = (hr_ctl*)p;
+            r.work.max_waves = max_waves;
+            r.work.max_intervals = HR_MAX_INTERVALS;
+            e = cudaMemsetAsync(r.work_mem, 0, total, s);
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
+        hr_region_dev& h = hdev[i];
+        memset(&h, 0, sizeof h);
+        h.shadow = r.shadow;
+        h.ring = r.ring;
+        h.n_words = r.desc.n_words;
+        h.ring_cap = r.ring_cap;
+        h.region = i;
+        h.geom.block_dim = r.desc.block_dim;
+        h.geom.warp_size = r.desc.warp_size;
+        h.geom.bd_magic = magic_for(r.desc.block_dim);
+        h.geom.ws_magic = magic_for(r.desc.warp_size);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_regions, hdev.data(), sizeof(hr_region_dev) * n_regions, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        st = cuda_status(e);
+        free_ctx(c);
+        return st;
+    }
+    *out = c;
+    return HR_OK;
+}
+
+static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                              uint32_t kernel_base, hr_stream_t stream, bool aggregate)
+{
+    if (!valid_region(ctx, region) || (n > 0 && !d_trace) || kernel_base > 0xFFFF) return HR_ERR_INVALID;
+    if (n >= (1ull << 40)) return HR_ERR_INVALID;
+    if (n == 0) return HR_OK;
+    RegionHost& r = ctx->regions[region];
+    cudaStream_t s = (cudaStream_t)stream;
+    ProfiledCall pc{};
+    if (ctx->profile) pc = take_events(ctx);
+    cudaEvent_t mid = ctx->profile ? pc.mid : nullptr;
+    if (ctx->profile) cudaEventRecord(pc.begin, s);
+    cudaError_t e = hr_launch_check(r.d, r.work, d_trace, n, kernel_base, ctx->d_table, aggregate,
+                                    hr_check_grid_size(aggregate), s, mid);
+    if (ctx->profile) {
+        cudaEventRecord(pc.end, s);
+        pc.launches = HR_LAUNCHES_PER_CHECK;
+        ctx->calls.push_back(pc);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_check_trace(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                                    hr_stream_t stream)
+{
+    return check_common(ctx, region, d_trace, n, 0, stream, true);
+}
+
+extern "C" hr_status hr_check_trace_kbase(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                                          uint32_t kernel_base, hr_stream_t stream)
+{
+    return check_common(ctx, region, d_trace, n, kernel_base, stream, true);
+}
+
+extern "C" hr_status hr_check_trace_plain(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                                          hr_stream_t stream)
+{
+    return check_common(ctx, region, d_trace, n, 0, stream, false);
+}
+
+extern "C" hr_status hr_sync(hr_ctx* ctx, uint32_t region, uint32_t scope, hr_stream_t stream)
+{
+    if (!valid_region(ctx, region) || scope != HR_SYNC_KERNEL) return HR_ERR_INVALID;
+    RegionHost& r = ctx->regions[region];
+    cudaStream_t s = (cudaStream_t)stream;
+    // device views (hand instrumentation) tag shadow values with kernel mod 8:
+    // when the next kernel starts a new group of 8, clear the shadow
+    cudaError_t e = cudaSuccess;
+    if (((r.kernel + 1) >> 3) != (r.kernel >> 3))
+        e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = hr_launch_sync_kernel(r.d, s);
+    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    if (e == cudaSuccess) r.kernel++;
+    return cuda_status(e);
+}
+
+static hr_status fetch_region(hr_ctx* ctx, uint32_t region, hr_region_dev* out)
+{
+    RegionHost& r = ctx->regions[region];
+    cudaError_t e = cudaEventSynchronize(r.done);
+    if (e == cudaSuccess) e = cudaMemcpy(out, r.d, sizeof *out, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_report(hr_ctx* ctx, uint32_t region, hr_race* host_out, uint64_t cap, uint64_t* n_total,
+                               uint32_t* flags)
+{
+    if (!valid_region(ctx, region) || (cap > 0 && !host_out)) return HR_ERR_INVALID;
+    hr_region_dev h;
+    hr_status st = fetch_region(ctx, region, &h);
+    if (st != HR_OK) return st;
+    const RegionHost& r = ctx->regions[region];
+    unsigned long long avail = h.n_races < r.ring_cap ? h.n_races : r.ring_cap;
+    unsigned long long ncopy = avail < cap ? avail : cap;
+    if (ncopy) {
+        cudaError_t e = cudaMemcpy(host_out, r.ring, ncopy * sizeof(hr_race), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (n_total) *n_total = h.n_races;
+    if (flags) *flags = h.flags | (h.n_races > cap ? HR_FLAG_TRUNCATED : 0u);
+    return (hr_status)h.error;
+}
+
+extern "C" hr_status hr_counters(hr_ctx* ctx, uint32_t region, uint64_t out[4])
+{
+    if (!valid_region(ctx, region) || !out) return HR_ERR_INVALID;
+    hr_region_dev h;
+    hr_status st = fetch_region(ctx, region, &h);
+    if (st != HR_OK) return st;
+    for (int i = 0; i < 4; ++i) out[i] = h.counters[i];
+    return HR_OK;
+}
+
+extern "C" hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream)
+{
+    if (!valid_region(ctx, region)) return HR_ERR_INVALID;
+    RegionHost& r = ctx->regions[region];
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = hr_launch_reset(r.d, r.shadow, r.desc.n_words, s);
+    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    r.kernel = 0;
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_destroy(hr_ctx* ctx)
+{
+    if (!ctx) return HR_ERR_INVALID;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(ctx);
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
+{
+    if (!valid_region(ctx, region) || !out) return HR_ERR_INVALID;
+    RegionHost& r = ctx->regions[region];
+    hr_region_dev* d = r.d;
+    out->shadow = r.shadow;
+    out->ring = r.ring;
+    out->n_races = &d->n_races;
+    out->error = &d->error;
+    out->flags = &d->flags;
+    out->table = ctx->d_table;
+    out->n_words = r.desc.n_words;
+    out->ring_cap = r.ring_cap;
+    out->geom.block_dim = r.desc.block_dim;
+    out->geom.warp_size = r.desc.warp_size;
+    out->geom.bd_magic = magic_for(r.desc.block_dim);
+    out->geom.ws_magic = magic_for(r.desc.warp_size);
+    out->kernel = r.kernel;
+    out->region = region;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_profile_enable(hr_ctx* ctx, int on)
+{
+    if (!ctx) return HR_ERR_INVALID;
+    ctx->profile = on != 0;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uint64_t* calls,
+                                     uint64_t* launches)
+{
+    if (!ctx) return HR_ERR_INVALID;
+    double ck = 0, pre = 0;
+    uint64_t nl = 0;
+    cudaError_t e = cudaSuccess;
+    for (auto& p : ctx->calls) {
+        float a = 0, b = 0;
+        if (e == cudaSuccess) e = cudaEventSynchronize(p.end);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&a, p.begin, p.mid);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, p.mid, p.end);
+        pre += a;
+        ck += b;
+        nl += p.launches;
+    }
+    if (check_ms) *check_ms = ck;
+    if (prepass_ms) *prepass_ms = pre;
+    if (calls) *calls = ctx->calls.size();
+    if (launches) *launches = nl;
+    ctx->spare.insert(ctx->spare.end(), ctx->calls.begin(), ctx->calls.end());
+    ctx->calls.clear();
+    return cuda_status(e);
+}
+
+extern "C" const char* hr_status_str(hr_status s)
+{
+    switch (s) {
+    case HR_OK: return "ok";
+    case HR_ERR_INVALID: return "invalid argument";
+    case HR_ERR_OOM: return "out of memory";
+    case HR_ERR_CUDA: return "CUDA runtime error";
+    case HR_ERR_ORDER: return "trace not sorted by (kernel, bc, wc) or older than the region's last record";
+    case HR_ERR_RANGE: return "word index out of range";
+    case HR_ERR_CLOCK_OVERFLOW: return "clock overflow";
+    case HR_ERR_CONTENTION: return "CAS retry cap reached";
+    case HR_ERR_TIMEOUT: return "bounded device wait expired";
+    case HR_ERR_UNSUPPORTED: return "unsupported record (partial-mask __syncwarp or unknown op)";
+    case HR_ERR_CAPACITY: return "too many waves in one call";
+    case HR_ERR_NOT_READY: return "region busy";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* hr_version(void) { return "hirace-gb300 0.1 (sm_103a)"; }

@@ -1,0 +1,214 @@
+"""Python binding of the C-ABI race checker (libhirace.so).
+
+Argument marshalling only: every step of the check runs in the library's
+CUDA kernels.  PyTorch is used for device memory and streams (tensors are
+passed by ``data_ptr()``, streams by ``cuda_stream``).  There is no CPU
+fallback: if the shared library is missing, importing the checker raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RACE_DTYPE = np.dtype([("word", "<u4"), ("tid", "<u4"), ("kernel", "<u2"), ("epoch", "<u2"),
+                       ("region", "<u2"), ("op", "u1"), ("prior", "u1")])
+assert RACE_DTYPE.itemsize == 16
+
+HR_OK = 0
+STATUS = {0: "HR_OK", 1: "HR_ERR_INVALID", 2: "HR_ERR_OOM", 3: "HR_ERR_CUDA", 4: "HR_ERR_ORDER",
+          5: "HR_ERR_RANGE", 6: "HR_ERR_CLOCK_OVERFLOW", 7: "HR_ERR_CONTENTION", 8: "HR_ERR_TIMEOUT",
+          9: "HR_ERR_UNSUPPORTED", 10: "HR_ERR_CAPACITY", 11: "HR_ERR_NOT_READY"}
+STATUS_CODE = {v: k for k, v in STATUS.items()}
+FLAG_TRUNCATED = 1
+SPACE_GLOBAL, SPACE_SHARED = 0, 1
+SYNC_KERNEL = 0
+
+
+class HrRegionDesc(ctypes.Structure):
+    _fields_ = [("n_words", ctypes.c_uint64), ("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32),
+                ("space", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("report_capacity", ctypes.c_uint64)]
+
+
+class HiRaceError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__("%s%s" % (STATUS.get(status, "status %d" % status), (": " + what) if what else ""))
+
+
+_lib = None
+
+
+def load_library():
+    """Load libhirace.so from the package directory (built by ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libhirace.so is not built (run __graft_entry__.build()); "
+                           "the checker has no CPU fallback")
+    lib = ctypes.CDLL(_build.LIB)
+    P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    lib.hr_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64, P]
+    lib.hr_check_trace.argtypes = [P, u32, P, u64, P]
+    lib.hr_check_trace_plain.argtypes = [P, u32, P, u64, P]
+    lib.hr_check_trace_kbase.argtypes = [P, u32, P, u64, u32, P]
+    lib.hr_sync.argtypes = [P, u32, u32, P]
+    lib.hr_report.argtypes = [P, u32, P, u64, ctypes.POINTER(u64), ctypes.POINTER(u32)]
+    lib.hr_counters.argtypes = [P, u32, ctypes.POINTER(u64 * 4)]
+    lib.hr_reset.argtypes = [P, u32, P]
+    lib.hr_destroy.argtypes = [P]
+    lib.hr_profile_enable.argtypes = [P, i32]
+    lib.hr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.hr_status_str.argtypes = [i32]
+    lib.hr_status_str.restype = ctypes.c_char_p
+    lib.hr_fsm_table.argtypes = [P, ctypes.POINTER(u32)]
+    lib.hr_fsm_state_name.argtypes = [u32]
+    lib.hr_fsm_state_name.restype = ctypes.c_char_p
+    lib.hr_version.restype = ctypes.c_char_p
+    for name in ("hr_init", "hr_check_trace", "hr_check_trace_plain", "hr_check_trace_kbase", "hr_sync", "hr_report", "hr_counters",
+                 "hr_reset", "hr_destroy", "hr_fsm_table", "hr_profile_enable", "hr_profile_read"):
+        getattr(lib, name).restype = i32
+    _lib = lib
+    return lib
+
+
+def fsm_table():
+    """(table[2048] uint8, n_states) of the flat FSM; host only, no GPU needed."""
+    lib = load_library()
+    out = np.zeros(2048, np.uint8)
+    n = ctypes.c_uint32(0)
+    rc = lib.hr_fsm_table(out.ctypes.data, ctypes.byref(n))
+    if rc:
+        raise HiRaceError(rc)
+    return out, int(n.value)
+
+
+def state_name(state: int) -> str:
+    return load_library().hr_fsm_state_name(state).decode()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr_and_count(trace):
+    if trace.device.type != "cuda":
+        raise ValueError("trace must be a CUDA tensor")
+    if not trace.is_contiguous():
+        raise ValueError("trace must be contiguous")
+    nbytes = trace.numel() * trace.element_size()
+    if nbytes % 16:
+        raise ValueError("trace size must be a multiple of 16 bytes")
+    return ctypes.c_void_p(trace.data_ptr()), nbytes // 16
+
+
+class Checker:
+    """One checker context with one shadow store per region.
+
+    ``regions`` is a list of dicts with keys n_words, block_dim and optional
+    warp_size (32), space (global), report_capacity (0 = the default).
+    """
+
+    def __init__(self, regions, report_capacity: int = 1 << 20, stream=None):
+        self._lib = load_library()
+        arr = (HrRegionDesc * len(regions))()
+        for i, r in enumerate(regions):
+            arr[i].n_words = int(r["n_words"])
+            arr[i].block_dim = int(r["block_dim"])
+            arr[i].warp_size = int(r.get("warp_size", 32))
+            arr[i].space = int(r.get("space", SPACE_GLOBAL))
+            arr[i].reserved = 0
+            arr[i].report_capacity = int(r.get("report_capacity", 0))
+        self.regions = [dict(r) for r in regions]
+        self.report_capacity = report_capacity
+        ctx = ctypes.c_void_p()
+        rc = self._lib.hr_init(ctypes.byref(ctx), arr, len(regions), report_capacity, _stream_handle(stream))
+        if rc:
+            raise HiRaceError(rc, "hr_init")
+        self._ctx = ctx
+
+    def _check(self, rc, what):
+        if rc:
+            raise HiRaceError(rc, what)
+
+    def check_trace(self, region: int, trace, stream=None, aggregate: bool = True, kernel_base: int = 0):
+        """Queue a check of a device-resident trace (16-byte records)."""
+        ptr, n = _ptr_and_count(trace)
+        st = _stream_handle(stream)
+        if kernel_base:
+            if not aggregate:
+                raise ValueError("kernel_base is only offered by the aggregated checker")
+            rc = self._lib.hr_check_trace_kbase(self._ctx, region, ptr, n, kernel_base, st)
+        else:
+            fn = self._lib.hr_check_trace if aggregate else self._lib.hr_check_trace_plain
+            rc = fn(self._ctx, region, ptr, n, st)
+        self._check(rc, "hr_check_trace")
+
+    def sync(self, region: int, stream=None):
+        self._check(self._lib.hr_sync(self._ctx, region, SYNC_KERNEL, _stream_handle(stream)), "hr_sync")
+
+    def report(self, region: int, cap: int | None = None):
+        """(races, status, n_total, flags); waits for the region's work."""
+        if cap is None:
+            cap = int(self.regions[region].get("report_capacity", 0) or self.report_capacity)
+        out = np.zeros(max(cap, 1), RACE_DTYPE)
+        n_total = ctypes.c_uint64(0)
+        flags = ctypes.c_uint32(0)
+        rc = self._lib.hr_report(self._ctx, region, out.ctypes.data, cap, ctypes.byref(n_total),
+                                 ctypes.byref(flags))
+        if rc in (STATUS_CODE["HR_ERR_INVALID"], STATUS_CODE["HR_ERR_CUDA"]):
+            raise HiRaceError(rc, "hr_report")
+        ring_cap = int(self.regions[region].get("report_capacity", 0) or self.report_capacity)
+        n = min(int(n_total.value), cap, ring_cap)
+        return out[:n], int(rc), int(n_total.value), int(flags.value)
+
+    def counters(self, region: int):
+        buf = (ctypes.c_uint64 * 4)()
+        self._check(self._lib.hr_counters(self._ctx, region, ctypes.byref(buf)), "hr_counters")
+        return dict(accesses=buf[0], cas=buf[1], retries=buf[2], merged=buf[3])
+
+    def reset(self, region: int, stream=None):
+        self._check(self._lib.hr_reset(self._ctx, region, _stream_handle(stream)), "hr_reset")
+
+    def profile(self, on: bool = True):
+        self._check(self._lib.hr_profile_enable(self._ctx, int(on)), "hr_profile_enable")
+
+    def profile_read(self):
+        """dict(check_ms, prepass_ms, calls, launches) summed since the last read."""
+        a, b = ctypes.c_double(0), ctypes.c_double(0)
+        c, d = ctypes.c_uint64(0), ctypes.c_uint64(0)
+        self._check(self._lib.hr_profile_read(self._ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                              ctypes.byref(d)), "hr_profile_read")
+        return dict(check_ms=a.value, prepass_ms=b.value, calls=c.value, launches=d.value)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.hr_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def race_keys(races) -> set:
+    """{(kernel, word, epoch)} of a race array."""
+    return {(int(k), int(w), int(e)) for k, w, e in zip(races["kernel"], races["word"], races["epoch"])}

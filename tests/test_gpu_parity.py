@@ -1,0 +1,203 @@
+"""GPU checker == CPU oracle, through the C-ABI.
+
+Race keys (kernel, word, epoch) must match bit for bit; the reported op must be
+one the oracle says can complete the first racy pair (several are possible
+inside one wave).  Every case runs the warp-aggregated and the plain kernel.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2401_04701_gb300 import tracegen as tg
+from tests import _cases as C
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hr():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2401_04701_gb300 import hirace
+    return hirace
+
+
+def to_dev(trace):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(trace).view(np.uint8)).cuda()
+
+
+def gpu_check(hr, trace, n_words, block_dim, warp_size=32, aggregate=True, chunks=None, cap=1 << 20):
+    with hr.Checker([dict(n_words=n_words, block_dim=block_dim, warp_size=warp_size)], report_capacity=cap) as ck:
+        if chunks is None:
+            ck.check_trace(0, to_dev(trace), aggregate=aggregate)
+        else:
+            for a, b in zip(chunks[:-1], chunks[1:]):
+                if b > a:
+                    ck.check_trace(0, to_dev(trace[a:b]), aggregate=aggregate)
+        races, status, n_total, flags = ck.report(0)
+        cnt = ck.counters(0)
+    return races, status, n_total, flags, cnt
+
+
+def assert_parity(O, hr, trace, n_words, block_dim, warp_size=32, aggregate=True, chunks=None):
+    bf = O.bruteforce(trace, block_dim, warp_size)
+    races, status, n_total, flags, _ = gpu_check(hr, trace, n_words, block_dim, warp_size, aggregate, chunks)
+    assert status == hr.HR_OK, hr.STATUS[status]
+    assert n_total == len(races) == len(bf)
+    assert hr.race_keys(races) == O.race_keys(bf)
+    ops = {(int(k), int(w)): int(m) for k, w, m in zip(bf["kernel"], bf["word"], bf["ops_mask"])}
+    for k, w, op in zip(races["kernel"], races["word"], races["op"]):
+        assert (ops[(int(k), int(w))] >> int(op)) & 1
+    return races
+
+
+@pytest.mark.parametrize("aggregate", [True, False])
+@pytest.mark.parametrize("name", ["listing1_no_sync", "listing2_block_sync", "listing2_one_block",
+                                  "listing3_multi_read"])
+def test_listings(oracle_mod, hr, name, aggregate):
+    g = C.load_golden(name)
+    tr = C.golden_trace(g)
+    races = assert_parity(oracle_mod, hr, tr, g["n_words"], g["block_dim"], g["warp_size"], aggregate)
+    assert hr.race_keys(races) == {tuple(x) for x in g["expected_races"]}
+
+
+@pytest.mark.parametrize("aggregate", [True, False])
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_exhaustive_universe(oracle_mod, hr, k, aggregate):
+    rng = np.random.default_rng(50 + k)
+    cases = C.exhaustive_cases(k, C.PHASES4)
+    base = C.combined_trace(cases, C.PHASES4)
+    for tr in (base, tg.shuffle_within_waves(base, rng)):
+        assert_parity(oracle_mod, hr, tr, len(cases), C.TOY_BLOCK_DIM, C.TOY_WARP, aggregate)
+
+
+@pytest.mark.parametrize("aggregate", [True, False])
+def test_random_deep_and_multi_kernel(oracle_mod, hr, aggregate):
+    rng = np.random.default_rng(60)
+    cases = C.random_cases(rng, 20000, 10, C.PHASES4)
+    assert_parity(oracle_mod, hr, C.combined_trace(cases, C.PHASES4), len(cases), C.TOY_BLOCK_DIM, C.TOY_WARP,
+                  aggregate)
+    for _ in range(10):
+        bd = int(rng.choice([3, 40, 64, 256]))
+        ws = int(rng.choice([2, 32]))
+        kernels = C.random_program(rng, n_threads=int(rng.integers(2, 600)), block_dim=bd, n_words=16,
+                                   n_acc=int(rng.integers(1, 3000)), n_st=int(rng.integers(0, 4)),
+                                   n_sw=int(rng.integers(0, 4)), n_kernels=int(rng.integers(1, 20)))
+        tr = tg.build_trace(kernels)
+        assert_parity(oracle_mod, hr, tr, 16, bd, ws, aggregate)
+
+
+@pytest.mark.parametrize("aggregate", [True, False])
+def test_tree_reduction_workload(oracle_mod, hr, aggregate):
+    tr, info = tg.gen_tree_reduction(tg.seed_for(1), inject=False)
+    races, status, n_total, _, _ = gpu_check(hr, tr, info["n_words"], info["block_dim"], aggregate=aggregate)
+    assert status == hr.HR_OK and n_total == 0
+    tr, info = tg.gen_tree_reduction(tg.seed_for(1), inject=True)
+    assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"], aggregate=aggregate)
+
+
+@pytest.mark.parametrize("aggregate", [True, False])
+def test_global_mix_small(oracle_mod, hr, aggregate):
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 1), inject=True, n_blocks=16)
+    races = assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"], aggregate=aggregate)
+    assert set(races["word"].tolist()) == set(info["injected"].tolist())
+
+
+def test_global_mix_full_size(oracle_mod, hr):
+    """The benchmark workload at full size (1024 x 256 threads, 2^26 words, 75.2M records)."""
+    tr, info = tg.gen_global_mix(tg.seed_for(2), inject=True)
+    races = assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"])
+    assert len(races) == len(info["injected"]) == 67108
+
+
+def test_chunked_calls_equal_one_call(oracle_mod, hr):
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 2), inject=True, n_blocks=8)
+    rng = np.random.default_rng(3)
+    cuts = np.sort(rng.integers(0, len(tr), 9))      # cuts land inside waves too
+    chunks = [0] + cuts.tolist() + [len(tr)]
+    assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"], chunks=chunks)
+
+
+def test_many_tiny_waves_and_ragged_tail(oracle_mod, hr):
+    # 2000 block epochs of a few records each; lengths not multiples of a tile
+    rng = np.random.default_rng(4)
+    progs = {}
+    for t in range(70):
+        ev = []
+        for e in range(2000):
+            if rng.random() < 0.3:
+                ev.append(("RWA"[int(rng.integers(0, 3))], int(rng.integers(0, 50))))
+            ev.append(("ST",))
+        progs[t] = ev
+    tr = tg.build_trace([progs])
+    assert_parity(oracle_mod, hr, tr, 50, 70, 32)
+
+
+def test_empty_and_single_record(oracle_mod, hr):
+    import torch
+    with hr.Checker([dict(n_words=4, block_dim=32)]) as ck:
+        ck.check_trace(0, torch.zeros(0, dtype=torch.uint8, device="cuda"))
+        one = tg.build_trace([{0: [("W", 3)]}])
+        ck.check_trace(0, to_dev(one))
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK and n_total == 0
+
+
+def test_kernel_base_and_sync(oracle_mod, hr):
+    tr = tg.build_trace([{0: [("W", 1)], 40: [("W", 1)]}])        # one race per launch
+    with hr.Checker([dict(n_words=4, block_dim=32)]) as ck:
+        for kb in range(0, 20):
+            ck.check_trace(0, to_dev(tr), kernel_base=kb)
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK
+        assert hr.race_keys(races) == {(kb, 1, 0) for kb in range(20)}
+        ck.sync(0)                       # kernel 19 ended: kernel 19 again is out of order
+        ck.check_trace(0, to_dev(tr), kernel_base=19)
+        _, status, _, _ = ck.report(0)
+        assert hr.STATUS[status] == "HR_ERR_ORDER"
+
+
+def test_errors_are_reported_not_faulted(hr):
+    good = tg.build_trace([{0: [("W", 1), ("ST",), ("R", 1)], 1: [("ST",), ("R", 2)]}])
+    cases = {}
+    bad = good.copy()
+    bad["word"][-1] = 100
+    cases["HR_ERR_RANGE"] = bad
+    cases["HR_ERR_ORDER"] = good[::-1].copy()
+    partial = tg.build_trace([{0: [("SW", tg.FLAG_PARTIAL_MASK), ("R", 1)]}])
+    cases["HR_ERR_UNSUPPORTED"] = partial
+    over = tg.build_trace([{0: [("R", 1)]}])
+    over["wc"] = 300
+    cases["HR_ERR_CLOCK_OVERFLOW"] = over
+    badop = good.copy()
+    badop["op"][0] = 9
+    cases["HR_ERR_UNSUPPORTED "] = badop
+    for want, tr in cases.items():
+        with hr.Checker([dict(n_words=4, block_dim=32)]) as ck:
+            ck.check_trace(0, to_dev(tr))
+            _, status, _, _ = ck.report(0)
+            assert hr.STATUS[status] == want.strip(), want
+
+
+def test_report_ring_overflow_keeps_exact_count(oracle_mod, hr):
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 3), inject=True, n_blocks=8)
+    n_expected = len(oracle_mod.bruteforce(tr, 256))
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=256, report_capacity=100)]) as ck:
+        ck.check_trace(0, to_dev(tr))
+        races, status, n_total, flags = ck.report(0)
+    assert status == hr.HR_OK and n_total == n_expected and len(races) == 100
+    assert flags & hr.FLAG_TRUNCATED
+
+
+def test_wave_capacity_error(hr, monkeypatch):
+    monkeypatch.setenv("HR_MAX_WAVES", "8")
+    tr = tg.build_trace([{t: [("R", t), ("ST",)] * 20 for t in range(4)}])
+    with hr.Checker([dict(n_words=8, block_dim=4)]) as ck:
+        ck.check_trace(0, to_dev(tr))
+        _, status, _, _ = ck.report(0)
+    assert hr.STATUS[status] == "HR_ERR_CAPACITY"
