@@ -206,6 +206,49 @@ hr_status hr_destroy(hr_ctx* ctx);
 hr_status hr_profile_enable(hr_ctx* ctx, int on);
 hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uint64_t* calls, uint64_t* launches);
 
+/*
+ * hr_check_trace_noalloc - the aggregated trace check for callers that cannot
+ * allocate device memory.  The paper has no counterpart: it is a deployment
+ * variant of hr_check_trace.  Callers that cannot call cudaMalloc include
+ * code running while another component owns the device memory budget (a
+ * framework's caching allocator or a fixed pool that already holds the free
+ * memory) and latency-critical paths where cudaMalloc/cudaFree would stall
+ * on an implicit device synchronisation.  No context is needed and nothing is
+ * allocated: no cudaMalloc, cudaFree or allocating library routine is called.
+ *   d_trace   n records, device memory, same rules as hr_check_trace
+ *   d_shadow  n_words 8-byte shadow values, caller-owned device memory, read
+ *             and updated in place; all zero = every word INIT (a fresh region)
+ *   d_races   race_cap race records (device), written from slot 0
+ *   d_result  device hr_result, overwritten: races found by this call (may
+ *             exceed race_cap), its sticky error, HR_FLAG_* flags
+ * The wave pre-pass scratch is a file-scope device array of
+ * HR_NOALLOC_SCRATCH_BYTES (451 KiB) inside the library; every GPU that loads
+ * the library holds it until the process exits.  Its limit: at most
+ * HR_NOALLOC_MAX_WAVES waves (distinct (kernel, bc, wc) keys) per call; a
+ * longer trace is rejected on the device with d_result->error ==
+ * HR_ERR_CAPACITY and nothing is checked.  The first call on each device
+ * looks up the array's device address and copies the FSM table into it with
+ * a synchronous cudaMemcpy, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call re-initialises what must start at zero); calls whose work
+ * overlaps on the GPU race on it, so serialise them.  Asynchronous on
+ * `stream` after the first call.  Returns HR_ERR_INVALID for bad arguments,
+ * HR_ERR_CUDA if a launch or the set-up fails; device-side errors go to
+ * d_result->error.
+ */
+#define HR_NOALLOC_MAX_WAVES 4096u
+#define HR_NOALLOC_SCRATCH_BYTES 461824u
+
+typedef struct hr_result {
+    uint64_t n_races;
+    uint32_t error;
+    uint32_t flags;
+} hr_result;
+
+hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n, uint64_t* d_shadow, uint64_t n_words,
+                                 uint32_t block_dim, uint32_t warp_size, hr_race* d_races, uint64_t race_cap,
+                                 hr_result* d_result, hr_stream_t stream);
+
 /* Static text for a status code. */
 const char* hr_status_str(hr_status s);
 

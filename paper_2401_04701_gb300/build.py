@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhirace.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hr_kernels.cu", "hr_api.cu", "hr_fsm.cpp"]
+SOURCES = ["hr_kernels.cu", "hr_api.cu", "hr_fsm.cpp", "hr_noalloc.cu"]
 
 
 def _nvcc() -> str:
