@@ -90,8 +90,8 @@ typedef struct hr_record {
  * One race report, 16 bytes: the first racy pair on `word` inside `kernel`
  * was completed by an access of thread `tid` doing `op` in block epoch
  * `epoch` (its bc).  `prior` is the FSM state the word held just before
- * (hr_fsm_state_name).  Races are reported once per (word, kernel) ("report
- * races on unique memory addresses", Sec. V-B).
+ * (hr_fsm_state_name).  Races are reported once per (word, kernel): the
+ * paper reports races per distinct address (Sec. V-B).
  */
 typedef struct hr_race {
     uint32_t word;
@@ -115,8 +115,8 @@ typedef struct hr_region_desc {
 
 /*
  * hr_init - create a checker context with one shadow store per region
- * (Sec. III-A: "we create a shadow[k] entry for each array element data[k]";
- * 8 bytes per word, Sec. IV-B).  Every shadow word starts in INIT.
+ * (Sec. III-A: one shadow entry per monitored array element; 8 bytes per
+ * word, Sec. IV-B).  Every shadow word starts in INIT.
  *   out              receives the context (host pointer; NULL on failure)
  *   regions          n_regions host descriptors
  *   report_capacity  default race records per region (>= 1)

@@ -7,8 +7,8 @@
  *    atomicCAS until it sticks.  The library's trace kernels use the same
  *    code through hr_fsm_step().
  * 2. Source-level instrumentation for hand-written kernels (Sec. IV-A: the
- *    wrapper "overrides relevant operators ... atomic functions and
- *    synchronization primitives"): call hr_access() next to every monitored
+ *    paper's wrapper intercepts indexing, atomics and barriers): call
+ *    hr_access() next to every monitored
  *    load, store or atomic, and use hr_syncthreads() / hr_syncwarp() in place
  *    of __syncthreads() / __syncwarp() so the thread-private clocks advance
  *    at the barrier (Sec. III-A Scenario 2).

@@ -12,9 +12,9 @@
  *  hro_validate     Recomputes every thread's block clock (bc) and warp clock
  *                   (wc) from its own __syncthreads / __syncwarp records and
  *                   checks they equal the clocks the producer wrote
- *                   (Sec. III, Scenario 2: "the thread-private block-scalar
- *                   clock (BC) updates" at the barrier; warp barriers add a
- *                   warp clock, Sec. III-B "Further Extension").
+ *                   (Sec. III-A, Scenario 2: each thread's private block
+ *                   clock advances when it passes a block barrier; warp
+ *                   barriers add a warp clock, Sec. III-B).
  *
  *  hro_bruteforce   The race definition itself (Sec. II-A): two accesses to
  *                   the same word race when they come from different threads,

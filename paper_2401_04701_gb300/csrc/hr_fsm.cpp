@@ -1,8 +1,8 @@
 // hr_fsm.cpp - builds the flat FSM transition table (host side).
 //
 // Sec. III: instead of the set of threads that touched a word, the FSM keeps
-// "the hierarchical scope shared by the accessing threads" plus the last
-// accessor; Sec. IV-B: the FSM is a flat array indexed by the old state and
+// the narrowest level of the thread hierarchy (thread, warp, block, grid) that
+// contains all of the word's accessors, plus the last accessor; Sec. IV-B: the FSM is a flat array indexed by the old state and
 // the transition labels (access, thread relation, sync status).  The paper's
 // own 25-state machine is not published (its Figs. 1 and 4 are absent), so
 // the states are derived here from what the race definition (Sec. II-A) and

@@ -131,7 +131,7 @@ def gen_tree_reduction(seed: int, inject: bool = True, segments: int = 48, block
     Epoch k (k = 0..log2(block_dim)-1) has stride s = block_dim/2 >> k; thread t < s
     reads words t and t+s of every segment and writes word t, ``reps`` times per
     epoch, with a __syncthreads() between epochs.  Injection: each (segment, epoch)
-    unit draws "double the active bound" (t < 2s, partner index mod block_dim) with
+    unit draws a doubled active bound (t < 2s, partner index mod block_dim) with
     probability ``p_unit``; each barrier draws "dropped" with the same probability;
     when ``force`` and a kind drew nothing, one unit of that kind is forced.
 
