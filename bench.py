@@ -90,9 +90,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_workload():
+def make_workload(n_blocks=1024):
     from paper_2401_04701_gb300 import tracegen as tg
-    trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True)
+    trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True, n_blocks=n_blocks)
     n_acc = int(np.count_nonzero(trace["op"] <= tg.OP_A))
     n_sync = len(trace) - n_acc
     return trace, info, n_acc, n_sync
@@ -145,7 +145,7 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     hirace.load_library()
 
-    trace, info, n_acc, n_sync = make_workload()
+    trace, info, n_acc, n_sync = make_workload(args.blocks)
     host = torch.from_numpy(trace.view(np.uint8)).pin_memory()
     d_trace = host.to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -184,6 +184,7 @@ def run_gpu(args, rank, world, local_rank):
     ms = start.elapsed_time(stop)
     prof = ck.profile_read()
     ck.profile(False)
+    counters = ck.counters(0)
     _, status, _, _ = ck.report(0)
     if status != hirace.HR_OK:
         raise SystemExit("timed steps ended with %s" % hirace.STATUS[status])
@@ -194,7 +195,7 @@ def run_gpu(args, rank, world, local_rank):
 
     # end to end through the C-ABI from pinned host memory: H2D of the trace,
     # reset, check, D2H of the race records
-    e2e_steps = max(1, min(args.steps, 10))
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 10))
     d2h = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -205,7 +206,7 @@ def run_gpu(args, rank, world, local_rank):
         races, status, n_total, _ = ck.report(0)
         d2h += races.nbytes + 64
     e2e_s = time.perf_counter() - t0
-    e2e_rate = world * n_acc * e2e_steps / e2e_s
+    e2e_rate = world * n_acc * e2e_steps / e2e_s if e2e_steps else None
 
     if rank != 0:
         ck.close()
@@ -216,7 +217,7 @@ def run_gpu(args, rank, world, local_rank):
     check_ms = prof["check_ms"] / max(1, prof["calls"])
     achieved = alg_bytes / (check_ms / 1e3) / 1e9
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and args.blocks == 1024:
         rate, dt, acc = cpu_oracle_rate(trace, info, n_acc)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "whole workload once (%d accesses, %.1f s), serial FSM oracle in C" % (acc, dt)}
@@ -233,7 +234,8 @@ def run_gpu(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
-                "d2h_bytes_per_step": int(d2h // e2e_steps)},
+                "d2h_bytes_per_step": int(d2h // max(1, e2e_steps))},
+        "fsm_counters": {k: int(v) for k, v in counters.items()},
         "gpu_launches": int(prof["launches"]),
         "clocks": clk,
     }
@@ -250,6 +252,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--blocks", type=int, default=1024,
+                    help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -135,7 +135,8 @@ hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_region
  *            passes this call; sorted by wave key (kernel, bc, wc), each
  *            thread's records in program order, kernels not older than the
  *            region's last processed record
- * Asynchronous.  Violations found on the device set the region's sticky
+ * d_trace must be 16-byte aligned.  Asynchronous.  Violations found on the
+ * device set the region's sticky
  * error (HR_ERR_ORDER, HR_ERR_RANGE, HR_ERR_CLOCK_OVERFLOW,
  * HR_ERR_CONTENTION, HR_ERR_UNSUPPORTED, HR_ERR_CAPACITY, HR_ERR_TIMEOUT);
  * checking of that region stops after the races found so far are reported

@@ -68,6 +68,8 @@ typedef struct hr_geom {
     uint32_t warp_size;
     uint64_t bd_magic;
     uint64_t ws_magic;
+    uint32_t bd_shift; /* log2(block_dim) when block_dim and warp_size are both powers of two, else ~0u */
+    uint32_t ws_shift; /* log2(warp_size) in that case */
 } hr_geom;
 
 /* Everything an instrumented kernel needs for one region; pass by value. */
@@ -99,6 +101,42 @@ static __device__ __forceinline__ uint32_t hr_fastdiv(uint32_t n, uint64_t magic
     return magic ? (uint32_t)__umul64hi(magic, (uint64_t)n) : n;
 }
 
+/* Thread relation of `tid` to the stored last accessor `otid` (compareTids). */
+static __device__ __forceinline__ uint32_t hr_thread_rel(uint32_t tid, uint32_t otid, const hr_geom& g)
+{
+    if (otid == tid) return HR_TREL_SAME;
+    if (g.bd_shift != ~0u) {
+        const uint32_t x = tid ^ otid;
+        if (x >> g.bd_shift) return HR_TREL_GRID;
+        const uint32_t m = g.block_dim - 1u;
+        return ((tid & m) >> g.ws_shift) == ((otid & m) >> g.ws_shift) ? HR_TREL_WARP : HR_TREL_BLOCK;
+    }
+    const uint32_t blk = hr_fastdiv(tid, g.bd_magic);
+    const uint32_t oblk = hr_fastdiv(otid, g.bd_magic);
+    if (oblk != blk) return HR_TREL_GRID;
+    const uint32_t warp = hr_fastdiv(tid - blk * g.block_dim, g.ws_magic);
+    const uint32_t owarp = hr_fastdiv(otid - oblk * g.block_dim, g.ws_magic);
+    return owarp == warp ? HR_TREL_WARP : HR_TREL_BLOCK;
+}
+
+/* First tid of the warp / block of `tid` (canonical identities of WARP and
+ * BLOCK states). */
+static __device__ __forceinline__ void hr_scope_heads(uint32_t tid, const hr_geom& g, uint32_t* warp_head,
+                                                      uint32_t* block_head)
+{
+    if (g.bd_shift != ~0u) {
+        const uint32_t loc = tid & (g.block_dim - 1u);
+        *block_head = tid - loc;
+        *warp_head = tid - (loc & (g.warp_size - 1u));
+        return;
+    }
+    const uint32_t blk = hr_fastdiv(tid, g.bd_magic);
+    const uint32_t loc = tid - blk * g.block_dim;
+    const uint32_t warp = hr_fastdiv(loc, g.ws_magic);
+    *block_head = tid - loc;
+    *warp_head = tid - (loc - warp * g.warp_size);
+}
+
 /* One FSM transition: fold access (tid, op, bc, wc) of kernel tag `ktag` into
  * the raw shadow value `o`.  `table` is the 2048-entry flat table (shared or
  * global memory).  Returns the new packed value; *raced is set to 1 + the old
@@ -109,23 +147,7 @@ static __device__ __forceinline__ uint64_t hr_fsm_step(uint64_t o, uint32_t tid,
 {
     uint32_t os = (uint32_t)(o >> HR_SH_STATE_SHIFT);
     if (os != HR_STATE_INIT && (uint32_t)((o >> HR_SH_KTAG_SHIFT) & 7u) != ktag) os = HR_STATE_INIT;
-    const uint32_t blk = hr_fastdiv(tid, g.bd_magic);
-    const uint32_t loc = tid - blk * g.block_dim;
-    const uint32_t warp = hr_fastdiv(loc, g.ws_magic);
-    const uint32_t lane = loc - warp * g.warp_size;
-    const uint32_t otid = (uint32_t)o;
-    uint32_t trel;
-    if (otid == tid) {
-        trel = HR_TREL_SAME;
-    } else {
-        const uint32_t oblk = hr_fastdiv(otid, g.bd_magic);
-        if (oblk != blk) {
-            trel = HR_TREL_GRID;
-        } else {
-            const uint32_t owarp = hr_fastdiv(otid - oblk * g.block_dim, g.ws_magic);
-            trel = owarp == warp ? HR_TREL_WARP : HR_TREL_BLOCK;
-        }
-    }
+    const uint32_t trel = hr_thread_rel(tid, (uint32_t)o, g);
     const uint32_t obc = (uint32_t)(o >> HR_SH_BC_SHIFT) & 0xFFFFu;
     const uint32_t owc = (uint32_t)(o >> HR_SH_WC_SHIFT) & 0xFFu;
     const uint32_t srel = bc != obc ? HR_SREL_BLOCK : (wc != owc ? HR_SREL_WARP : HR_SREL_UNSYNC);
@@ -133,12 +155,14 @@ static __device__ __forceinline__ uint64_t hr_fsm_step(uint64_t o, uint32_t tid,
     const uint32_t ns = e & 31u;
     const uint32_t lvl = e >> 5;
     uint64_t n = ((uint64_t)ns << HR_SH_STATE_SHIFT) | ((uint64_t)ktag << HR_SH_KTAG_SHIFT);
-    if (lvl == HR_LVL_THREAD)
-        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT) | tid;
-    else if (lvl == HR_LVL_WARP)
-        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT) | (tid - lane);
-    else if (lvl == HR_LVL_BLOCK)
-        n |= ((uint64_t)bc << HR_SH_BC_SHIFT) | (tid - loc);
+    if (lvl >= HR_LVL_THREAD && lvl <= HR_LVL_BLOCK) {
+        uint32_t wh, bh;
+        hr_scope_heads(tid, g, &wh, &bh);
+        const uint32_t who = lvl == HR_LVL_THREAD ? tid : (lvl == HR_LVL_WARP ? wh : bh);
+        const uint64_t clk = lvl == HR_LVL_BLOCK ? ((uint64_t)bc << HR_SH_BC_SHIFT)
+                                                 : (((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT));
+        n |= clk | who;
+    }
     if (ns == HR_STATE_RACE && os != HR_STATE_RACE) *raced = 1u + os;
     return n;
 }

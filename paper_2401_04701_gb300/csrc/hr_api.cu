@@ -22,8 +22,6 @@ struct RegionHost {
     cudaEvent_t done = nullptr;           // recorded after every call on the region
 };
 
-uint64_t magic_for(uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; }
-
 hr_status cuda_status(cudaError_t e)
 {
     if (e == cudaSuccess) return HR_OK;
@@ -155,10 +153,7 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         h.n_words = r.desc.n_words;
         h.ring_cap = r.ring_cap;
         h.region = i;
-        h.geom.block_dim = r.desc.block_dim;
-        h.geom.warp_size = r.desc.warp_size;
-        h.geom.bd_magic = magic_for(r.desc.block_dim);
-        h.geom.ws_magic = magic_for(r.desc.warp_size);
+        h.geom = hr_make_geom(r.desc.block_dim, r.desc.warp_size);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_regions, hdev.data(), sizeof(hr_region_dev) * n_regions, cudaMemcpyHostToDevice, s);
@@ -176,6 +171,7 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
                               uint32_t kernel_base, hr_stream_t stream, bool aggregate)
 {
     if (!valid_region(ctx, region) || (n > 0 && !d_trace) || kernel_base > 0xFFFF) return HR_ERR_INVALID;
+    if (((uintptr_t)d_trace & 15u) != 0) return HR_ERR_INVALID;  // records are copied in 16-byte units
     if (n >= (1ull << 40)) return HR_ERR_INVALID;
     if (n == 0) return HR_OK;
     RegionHost& r = ctx->regions[region];
@@ -298,10 +294,7 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     out->table = ctx->d_table;
     out->n_words = r.desc.n_words;
     out->ring_cap = r.ring_cap;
-    out->geom.block_dim = r.desc.block_dim;
-    out->geom.warp_size = r.desc.warp_size;
-    out->geom.bd_magic = magic_for(r.desc.block_dim);
-    out->geom.ws_magic = magic_for(r.desc.warp_size);
+    out->geom = hr_make_geom(r.desc.block_dim, r.desc.warp_size);
     out->kernel = r.kernel;
     out->region = region;
     return HR_OK;

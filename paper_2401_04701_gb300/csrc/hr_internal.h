@@ -6,6 +6,27 @@
 #include "../../include/hirace.h"
 #include "../../include/hirace_device.cuh"
 
+// Geometry with exact reciprocals and, when both sizes are powers of two, shifts.
+inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size)
+{
+    auto magic = [](uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; };
+    auto log2_exact = [](uint32_t d) -> uint32_t {
+        if (d == 0 || (d & (d - 1))) return ~0u;
+        uint32_t s = 0;
+        while ((1u << s) < d) ++s;
+        return s;
+    };
+    hr_geom g{};
+    g.block_dim = block_dim;
+    g.warp_size = warp_size;
+    g.bd_magic = magic(block_dim);
+    g.ws_magic = magic(warp_size);
+    const uint32_t bs = log2_exact(block_dim), ws = log2_exact(warp_size);
+    g.bd_shift = (bs != ~0u && ws != ~0u) ? bs : ~0u;
+    g.ws_shift = (bs != ~0u && ws != ~0u) ? ws : ~0u;
+    return g;
+}
+
 // Per-region state in device memory.
 struct hr_region_dev {
     unsigned long long* shadow;   // n_words shadow values
@@ -55,9 +76,11 @@ struct hr_work {
     unsigned int max_intervals;
 };
 
-constexpr int HR_THREADS = 256;                // threads per CTA of the checker
-constexpr int HR_RPT = 8;                      // records per thread per tile
-constexpr int HR_TILE = HR_THREADS * HR_RPT;   // records per tile (one wave per tile)
+constexpr int HR_CONSUMERS = 8;                          // consumer warps per CTA
+constexpr int HR_THREADS = (HR_CONSUMERS + 1) * 32;      // + one producer warp
+constexpr int HR_RPL = 4;                                // records per consumer lane per tile
+constexpr int HR_TILE = HR_CONSUMERS * 32 * HR_RPL;      // records per tile (one wave per tile)
+constexpr int HR_RING = 2;                               // tiles in flight in shared memory
 constexpr unsigned HR_CLEAR_WORDS = 1u << 16;  // shadow words per clear item
 constexpr unsigned HR_MAX_INTERVALS = 1u << 16;
 constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;

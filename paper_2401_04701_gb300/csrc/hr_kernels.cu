@@ -233,14 +233,122 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
 }
 
 // ------------------------------------------------------------ the FSM checker
+//
+// Warp-specialised persistent CTAs.  One producer warp (lane 0) takes work
+// items in ticket order and streams each tile of records into a shared-memory
+// ring with a bulk asynchronous copy (cp.async.bulk, completion on an mbarrier,
+// L2 evict-first so the stream does not push shadow lines out of L2).  Eight
+// consumer warps take the tiles from the ring, release the slot as soon as
+// their records sit in registers, and apply them to the shadow.  A tile of
+// wave w may only touch the shadow once every tile of the previous stage is
+// done (per-warp completion counts with release/acquire); while it waits, the
+// warp already loads its shadow words and then validates them with the CAS.
+
+struct TileInfo {
+    unsigned long long rb, re, key;  // record range and wave key of the tile
+    unsigned stage, type, item, valid;
+    unsigned skip, prev_need, pad0, pad1;
+};
 
 struct Acc {
     unsigned tid;
     unsigned op;
 };
 
+constexpr size_t SMEM_REC = (size_t)HR_RING * HR_TILE * sizeof(uint4);
+constexpr size_t SMEM_ACC = (size_t)HR_CONSUMERS * HR_RPL * 32 * sizeof(Acc);
+constexpr size_t SMEM_BYTES = SMEM_REC + 2048 + SMEM_ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded mbarrier wait: gives up (and raises the abort flag) after HR_WAIT_NS
+// or when another CTA aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* abort_flag, unsigned* err)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*(volatile unsigned*)abort_flag) return false;
+        if (globaltimer() - t0 > HR_WAIT_NS) {
+            atomicExch(abort_flag, 1u);
+            hr_set_error(err, HR_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Bounded wait until a stage's completion count reaches `need`.
+__device__ __forceinline__ bool stage_wait(const unsigned* done, unsigned need, unsigned* abort_flag, unsigned* err)
+{
+    const unsigned long long t0 = globaltimer();
+    unsigned ns = 64;
+    while (ld_acquire_u32(done) < need) {
+        if (*(volatile unsigned*)abort_flag) return false;
+        if (globaltimer() - t0 > HR_WAIT_NS) {
+            atomicExch(abort_flag, 1u);
+            hr_set_error(err, HR_ERR_TIMEOUT);
+            return false;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+    return true;
+}
+
 // Fold the accesses of one lane group (lanes in `grp`, in lane order) into o.
-__device__ __forceinline__ unsigned long long fold_group(unsigned long long o, unsigned grp, const Acc* acc,
+__device__ __noinline__ unsigned long long fold_group(unsigned long long o, unsigned grp, const Acc* acc,
                                                          unsigned bc, unsigned wc, unsigned ktag,
                                                          const hr_geom& g, const unsigned char* table,
                                                          unsigned* raced, unsigned* who)
@@ -258,108 +366,192 @@ __device__ __forceinline__ unsigned long long fold_group(unsigned long long o, u
     return o;
 }
 
-template <bool AGG>
-__global__ void __launch_bounds__(HR_THREADS, 2) hr_check_kernel(hr_region_dev* __restrict__ region, hr_work w,
-                                                              const hr_record* __restrict__ trace,
-                                                              const unsigned char* __restrict__ gtable,
-                                                              unsigned long long kb)
+// Cold path: the first CAS lost a race (or validated a stale speculative
+// load).  Re-fold from the value it returned until a CAS sticks or the retry
+// cap is reached.  Returns the number of extra CAS attempts; *ok tells success.
+__device__ __noinline__ unsigned retry_cas(unsigned long long* p, unsigned long long seen, unsigned tid, unsigned op,
+                                           unsigned grp, const Acc* acc, unsigned bc, unsigned wc, unsigned ktag,
+                                           const hr_geom& g, const unsigned char* table, unsigned* raced,
+                                           unsigned* who, bool* ok)
 {
-    __shared__ unsigned char s_table[2048];
-    __shared__ Acc s_acc[HR_THREADS / 32][HR_RPT][32];
-    __shared__ unsigned s_item, s_stage, s_skip;
-    __shared__ unsigned long long s_cnt[4];
+    const unsigned lane = threadIdx.x & 31;
+    unsigned attempts = 0;
+    for (int tries = 0; tries < HR_CAS_RETRY_CAP; ++tries) {
+        const unsigned long long o = seen;
+        *raced = 0;
+        *who = lane;
+        const unsigned long long n = grp == (1u << lane) ? hr_fsm_step(o, tid, op, bc, wc, ktag, g, table, raced)
+                                                         : fold_group(o, grp, acc, bc, wc, ktag, g, table, raced, who);
+        if (n == o) {
+            *ok = true;
+            return attempts;
+        }
+        attempts++;
+        seen = atomicCAS(p, o, n);
+        if (seen == o) {
+            *ok = true;
+            return attempts;
+        }
+    }
+    *ok = false;
+    return attempts;
+}
 
-    reinterpret_cast<uint2*>(s_table)[threadIdx.x] = reinterpret_cast<const uint2*>(gtable)[threadIdx.x];
-    if (threadIdx.x < 4) s_cnt[threadIdx.x] = 0;
+__device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record* trace, unsigned long long kb,
+                              uint4* s_rec, TileInfo* s_info, uint64_t* s_full, uint64_t* s_empty)
+{
+    const uint64_t pol = policy_evict_first();
+    const unsigned total = w.ctl->total_items;
+    unsigned s = 0, s_begin = 0, s_end = 0, type = 0, prev_need = 0;
+    unsigned long long w_start = 0, w_end = 0, key = 0;
+    bool have = false;
+    for (unsigned it = 0;; ++it) {
+        const unsigned b = it % HR_RING;
+        if (it >= HR_RING &&
+            !mbar_wait(&s_empty[b], ((it / HR_RING) - 1) & 1u, &w.ctl->abort, &region->error)) {
+            s_info[b].valid = 0;
+            mbar_arrive(&s_full[b]);
+            return;
+        }
+        const unsigned t = atomicAdd(&w.ctl->ticket, 1u);
+        if (t >= total || *(volatile unsigned*)&w.ctl->abort) {
+            s_info[b].valid = 0;
+            mbar_arrive(&s_full[b]);
+            return;
+        }
+        if (!have || t >= s_end) {  // move to the stage holding ticket t
+            if (!have) s = 0;
+            while (w.stages[s + 1].item_begin <= t) ++s;
+            const hr_stage st = w.stages[s];
+            s_begin = st.item_begin;
+            s_end = w.stages[s + 1].item_begin;
+            type = st.type;
+            prev_need = s ? (s_begin - w.stages[s - 1].item_begin) * HR_CONSUMERS : 0u;
+            w_start = w.wave_start[st.wave];
+            w_end = w.wave_start[st.wave + 1];
+            key = w.wave_key[st.wave];  // already rebased by the pre-pass
+            have = true;
+        }
+        TileInfo info;
+        info.valid = 1;
+        info.stage = s;
+        info.type = type;
+        info.item = t - s_begin;
+        info.prev_need = prev_need;
+        info.skip = *(volatile unsigned*)&region->error != 0;
+        info.key = key;
+        info.rb = w_start + (unsigned long long)info.item * HR_TILE;
+        info.re = min(info.rb + HR_TILE, w_end);
+        s_info[b] = info;
+        if (type == HR_STAGE_RECORDS && !info.skip) {
+            const uint32_t bytes = (uint32_t)(info.re - info.rb) * (uint32_t)sizeof(hr_record);
+            mbar_arrive_tx(&s_full[b], bytes);
+            bulk_g2s(s_rec + (size_t)b * HR_TILE, trace + info.rb, bytes, &s_full[b], pol);
+        } else {
+            mbar_arrive(&s_full[b]);
+        }
+    }
+}
+
+template <bool AGG>
+__global__ void __launch_bounds__(HR_THREADS, 3) hr_check_kernel(hr_region_dev* __restrict__ region, hr_work w,
+                                                                 const hr_record* __restrict__ trace,
+                                                                 const unsigned char* __restrict__ gtable,
+                                                                 unsigned long long kb)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint4* s_rec = reinterpret_cast<uint4*>(smem);
+    unsigned char* s_table = smem + SMEM_REC;
+    Acc* s_acc = reinterpret_cast<Acc*>(s_table + 2048);
+    TileInfo* s_info = reinterpret_cast<TileInfo*>(smem + SMEM_REC + 2048 + SMEM_ACC);
+    uint64_t* s_full = reinterpret_cast<uint64_t*>(s_info + HR_RING);
+    uint64_t* s_empty = s_full + HR_RING;
+
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
+        reinterpret_cast<uint2*>(s_table)[i] = reinterpret_cast<const uint2*>(gtable)[i];
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < HR_RING; ++b) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_empty[b], HR_CONSUMERS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (wid == HR_CONSUMERS) {
+        if (lane == 0) producer_loop(w, region, trace, kb, s_rec, s_info, s_full, s_empty);
+        return;
+    }
+
+    // ---- consumer warp
     const hr_geom g = region->geom;
     unsigned long long* __restrict__ shadow = region->shadow;
     const unsigned long long n_words = region->n_words;
-    const unsigned total = w.ctl->total_items;
-    unsigned hint = 0;
+    Acc* my_acc = s_acc + (size_t)wid * HR_RPL * 32;
+    int known = -1;  // highest stage index this warp has seen complete
     unsigned long long c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
-    __syncthreads();
 
-    while (true) {
-        if (threadIdx.x == 0) {
-            const unsigned t = atomicAdd(&w.ctl->ticket, 1u);
-            s_item = t;
-            if (t < total) {
-                unsigned s = hint;
-                while (w.stages[s + 1].item_begin <= t) ++s;
-                s_stage = s;
-            }
-        }
-        __syncthreads();
-        const unsigned t = s_item;
-        if (t >= total) break;
-        const unsigned s = s_stage;
-        hint = s;
-        const hr_stage st = w.stages[s];
-        const unsigned item = t - st.item_begin;
-
-        // stage the tile's records in registers before waiting on the previous stage
-        uint4 rec[HR_RPT];
-        unsigned long long rb = 0, re = 0, wkey = 0;
-        if (st.type == HR_STAGE_RECORDS) {
-            rb = w.wave_start[st.wave] + (unsigned long long)item * HR_TILE;
-            re = min(rb + HR_TILE, w.wave_start[st.wave + 1]);
-            wkey = w.wave_key[st.wave];
+    for (unsigned it = 0;; ++it) {
+        const unsigned b = it % HR_RING;
+        if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, &region->error)) break;
+        const TileInfo info = s_info[b];
+        if (!info.valid) break;
+        const bool records = info.type == HR_STAGE_RECORDS && !info.skip;
+        uint4 rec[HR_RPL];
+        const unsigned base = wid * 32 * HR_RPL + lane;
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k) {
-                const unsigned long long r = rb + (unsigned long long)k * HR_THREADS + threadIdx.x;
-                rec[k] = r < re ? ld_stream(trace + r) : make_uint4(0, 0, 0, 0xFFFFFFFFu);
-            }
+        for (int k = 0; k < HR_RPL; ++k) {
+            const unsigned idx = base + k * 32;
+            rec[k] = (records && info.rb + idx < info.re) ? s_rec[(size_t)b * HR_TILE + idx]
+                                                          : make_uint4(0, 0, 0, 0xFFFFFFFFu);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[b]);  // the slot may be refilled now
+
+        const unsigned s = info.stage;
+        bool ready = s == 0 || (int)s - 1 <= known;
+        if (!ready) {
+            unsigned r = 0;
+            if (lane == 0) r = ld_acquire_u32(&w.stages[s - 1].done) >= info.prev_need;
+            ready = __shfl_sync(0xffffffffu, r, 0) != 0;
+            __syncwarp();
+            if (ready) known = (int)s - 1;
         }
 
-        if (threadIdx.x == 0) {
-            bool ok = true;
-            if (s > 0) {
-                const unsigned need = st.item_begin - w.stages[s - 1].item_begin;
-                const unsigned long long t0 = globaltimer();
-                unsigned ns = 32;
-                while (ld_acquire_u32(&w.stages[s - 1].done) < need) {
-                    if (*(volatile unsigned*)&w.ctl->abort) { ok = false; break; }
-                    if (globaltimer() - t0 > HR_WAIT_NS) {
-                        atomicExch(&w.ctl->abort, 1u);
-                        hr_set_error(&region->error, HR_ERR_TIMEOUT);
-                        ok = false;
-                        break;
-                    }
-                    __nanosleep(ns);
-                    if (ns < 2048) ns <<= 1;
-                }
+        if (info.type == HR_STAGE_CLEAR && !info.skip) {
+            if (!ready) {
+                bool ok = true;
+                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                __syncwarp();
+                if (!ok) break;
+                known = (int)s - 1;
             }
-            s_skip = ok ? (*(volatile unsigned*)&region->error != 0 ? 1u : 0u) : 2u;
-        }
-        __syncthreads();
-        const unsigned skip = s_skip;
-        if (skip == 2) break;  // aborted: a bounded wait expired somewhere
-
-        if (!skip && st.type == HR_STAGE_CLEAR) {
-            const unsigned long long wb = (unsigned long long)item * HR_CLEAR_WORDS;
-            const unsigned long long we = min(n_words, wb + HR_CLEAR_WORDS);
-            for (unsigned long long i = wb + 2ull * threadIdx.x; i < we; i += 2ull * HR_THREADS) {
+            const unsigned long long span = HR_CLEAR_WORDS / HR_CONSUMERS;
+            const unsigned long long wb = (unsigned long long)info.item * HR_CLEAR_WORDS + wid * span;
+            const unsigned long long we = min(n_words, wb + span);
+            for (unsigned long long i = wb + 2ull * lane; i < we; i += 64ull) {
                 if (i + 1 < we)
                     *reinterpret_cast<ulonglong2*>(shadow + i) = make_ulonglong2(0ull, 0ull);
                 else
                     shadow[i] = 0ull;
             }
-        } else if (!skip) {
+        } else if (records) {
+            const unsigned long long wkey = info.key;
             const unsigned bc = (unsigned)(wkey >> 16) & 0xFFFFu;
             const unsigned wc = (unsigned)wkey & 0xFFFFu;
             const unsigned kern = (unsigned)(wkey >> 32);
             const unsigned ktag = kern & 7u;
             unsigned err = 0;
-            if (wc > HR_WC_MAX) err = HR_ERR_CLOCK_OVERFLOW;
-            unsigned word[HR_RPT], grp[HR_RPT];
-            bool act[HR_RPT];
+            unsigned word[HR_RPL], grp[HR_RPL], tidv[HR_RPL], opv[HR_RPL];
+            bool act[HR_RPL];
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k) {
+            for (int k = 0; k < HR_RPL; ++k) {
                 const uint4 v = rec[k];
                 const unsigned op = (v.w >> 16) & 0xFFu;
                 const unsigned flags = v.w >> 24;
-                const bool in = rb + (unsigned long long)k * HR_THREADS + threadIdx.x < re;
+                const bool in = info.rb + base + k * 32 < info.re;
                 const unsigned long long key = (((unsigned long long)(v.w & 0xFFFFu) << 32) |
                                                 ((unsigned long long)(v.z >> 16) << 16) | (v.z & 0xFFFFu)) + kb;
                 bool a = in && op <= HR_A;
@@ -373,78 +565,89 @@ __global__ void __launch_bounds__(HR_THREADS, 2) hr_check_kernel(hr_region_dev* 
                 a = a && key == wkey && v.x < n_words && wc <= HR_WC_MAX;
                 act[k] = a;
                 word[k] = v.x;
-                s_acc[wid][k][lane] = Acc{v.y, op};
+                tidv[k] = v.y;
+                opv[k] = op;
+                grp[k] = 1u << lane;
                 if (AGG) {
-                    const unsigned long long mk = a ? (unsigned long long)v.x : (0xFFFFFFFF00000000ull | lane);
-                    grp[k] = __match_any_sync(0xffffffffu, mk);
-                    if (a && (__ffs(grp[k]) - 1) != lane) {
-                        act[k] = false;  // folded by the group leader
-                        c_merged++;
+                    const unsigned am = __ballot_sync(0xffffffffu, a);
+                    // cheap screen: only run the match when a neighbour lane repeats the word
+                    const unsigned up = __shfl_up_sync(0xffffffffu, v.x, 1);
+                    const bool adj = a && lane > 0 && ((am >> (lane - 1)) & 1u) && up == v.x;
+                    if (__any_sync(0xffffffffu, adj)) {
+                        my_acc[k * 32 + lane] = Acc{v.y, op};
+                        const unsigned m = __match_any_sync(0xffffffffu, a ? v.x : 0xFFFFFFFFu) & am;
+                        if (a) {
+                            grp[k] = m;
+                            if ((unsigned)(__ffs(m) - 1) != lane) {
+                                act[k] = false;  // folded by the group leader
+                                c_merged++;
+                            }
+                        }
                     }
-                } else {
-                    grp[k] = 1u << lane;
                 }
             }
+            if (wc > HR_WC_MAX) err = HR_ERR_CLOCK_OVERFLOW;
             if (err) hr_set_error(&region->error, err);
             __syncwarp();
 
-            unsigned long long o[HR_RPT], nv[HR_RPT], prev[HR_RPT];
-            unsigned raced[HR_RPT], who[HR_RPT];
+            unsigned long long o[HR_RPL], nv[HR_RPL];
+            unsigned raced[HR_RPL], who[HR_RPL];
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k)
+            for (int k = 0; k < HR_RPL; ++k)
                 if (act[k]) o[k] = hr_ld_relaxed(shadow + word[k]);
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k) {
+            for (int k = 0; k < HR_RPL; ++k) {
                 raced[k] = 0;
                 who[k] = lane;
                 if (act[k]) {
-                    c_acc += __popc(grp[k]);
-                    nv[k] = fold_group(o[k], grp[k], s_acc[wid][k], bc, wc, ktag, g, s_table, &raced[k], &who[k]);
+                    if (grp[k] == (1u << lane)) {
+                        c_acc++;
+                        nv[k] = hr_fsm_step(o[k], tidv[k], opv[k], bc, wc, ktag, g, s_table, &raced[k]);
+                    } else {
+                        c_acc += __popc(grp[k]);
+                        nv[k] = fold_group(o[k], grp[k], my_acc + k * 32, bc, wc, ktag, g, s_table, &raced[k],
+                                           &who[k]);
+                    }
                 }
             }
+            bool force = false;
+            if (!ready) {  // the loads above ran ahead of the previous stage: validate them by CAS
+                bool ok = true;
+                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                __syncwarp();
+                if (!ok) break;
+                known = (int)s - 1;
+                force = true;
+            }
+            bool need[HR_RPL];
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k)
-                if (act[k] && nv[k] != o[k]) prev[k] = atomicCAS(shadow + word[k], o[k], nv[k]);
+            for (int k = 0; k < HR_RPL; ++k) {
+                need[k] = act[k] && (force || nv[k] != o[k]);
+                if (need[k]) nv[k] = atomicCAS(shadow + word[k], o[k], nv[k]);  // nv now holds the value seen
+            }
 #pragma unroll
-            for (int k = 0; k < HR_RPT; ++k) {
-                if (!act[k]) continue;
+            for (int k = 0; k < HR_RPL; ++k) {
+                if (!need[k]) continue;
+                c_cas++;
                 bool done = nv[k] == o[k];
                 if (!done) {
-                    c_cas++;
-                    done = prev[k] == o[k];
-                    int tries = 0;
-                    while (!done && tries < HR_CAS_RETRY_CAP) {
-                        ++tries;
-                        c_retry++;
-                        o[k] = prev[k];
-                        raced[k] = 0;
-                        nv[k] = fold_group(o[k], grp[k], s_acc[wid][k], bc, wc, ktag, g, s_table, &raced[k],
-                                           &who[k]);
-                        if (nv[k] == o[k]) {
-                            done = true;
-                            break;
-                        }
-                        c_cas++;
-                        prev[k] = atomicCAS(shadow + word[k], o[k], nv[k]);
-                        done = prev[k] == o[k];
-                    }
+                    c_retry++;
+                    c_cas += retry_cas(shadow + word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc, wc, ktag,
+                                       g, s_table, &raced[k], &who[k], &done);
                     if (!done) hr_set_error(&region->error, HR_ERR_CONTENTION);
-                    if (done && raced[k]) {
-                        const Acc a = s_acc[wid][k][who[k]];
-                        hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, word[k],
-                                       a.tid, kern, bc, region->region, a.op, raced[k] - 1u);
-                    }
+                }
+                if (done && raced[k]) {
+                    const unsigned rt = who[k] == lane ? tidv[k] : my_acc[k * 32 + who[k]].tid;
+                    const unsigned ro = who[k] == lane ? opv[k] : my_acc[k * 32 + who[k]].op;
+                    hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, word[k], rt,
+                                   kern, bc, region->region, ro, raced[k] - 1u);
                 }
             }
-            __syncwarp();
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(&w.stages[s].done, 1u);
-        }
+        __syncwarp();
+        if (lane == 0) red_release_add(&w.stages[s].done, 1u);
     }
-    // counters: one atomic per CTA
     for (int o2 = 16; o2 > 0; o2 >>= 1) {
         c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o2);
         c_cas += __shfl_xor_sync(0xffffffffu, c_cas, o2);
@@ -452,13 +655,11 @@ __global__ void __launch_bounds__(HR_THREADS, 2) hr_check_kernel(hr_region_dev* 
         c_merged += __shfl_xor_sync(0xffffffffu, c_merged, o2);
     }
     if (lane == 0) {
-        atomicAdd(&s_cnt[0], c_acc);
-        atomicAdd(&s_cnt[1], c_cas);
-        atomicAdd(&s_cnt[2], c_retry);
-        atomicAdd(&s_cnt[3], c_merged);
+        if (c_acc) atomicAdd(&region->counters[0], c_acc);
+        if (c_cas) atomicAdd(&region->counters[1], c_cas);
+        if (c_retry) atomicAdd(&region->counters[2], c_retry);
+        if (c_merged) atomicAdd(&region->counters[3], c_merged);
     }
-    __syncthreads();
-    if (threadIdx.x < 4 && s_cnt[threadIdx.x]) atomicAdd(&region->counters[threadIdx.x], s_cnt[threadIdx.x]);
 }
 
 __global__ void hr_sync_kernel(hr_region_dev* region)
@@ -490,10 +691,13 @@ int hr_check_grid_size(bool aggregate)
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (aggregate)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<true>, HR_THREADS, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<false>, HR_THREADS, 0);
+    if (aggregate) {
+        cudaFuncSetAttribute(hr_check_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<true>, HR_THREADS, SMEM_BYTES);
+    } else {
+        cudaFuncSetAttribute(hr_check_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<false>, HR_THREADS, SMEM_BYTES);
+    }
     if (per_sm < 1) per_sm = 1;
     cached = sms * per_sm;
     return cached;
@@ -514,9 +718,9 @@ cudaError_t hr_launch_check(hr_region_dev* d_region, const hr_work& w, const hr_
     hr_build_stages<<<1, 1024, 0, stream>>>(w, d_region);
     if (before_check) cudaEventRecord(before_check, stream);
     if (aggregate)
-        hr_check_kernel<true><<<grid, HR_THREADS, 0, stream>>>(d_region, w, trace, d_table, kb);
+        hr_check_kernel<true><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_region, w, trace, d_table, kb);
     else
-        hr_check_kernel<false><<<grid, HR_THREADS, 0, stream>>>(d_region, w, trace, d_table, kb);
+        hr_check_kernel<false><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_region, w, trace, d_table, kb);
     return cudaGetLastError();
 }
 

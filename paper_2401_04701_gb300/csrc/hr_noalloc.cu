@@ -86,8 +86,6 @@ __global__ void hr_noalloc_end(const hr_region_dev* region, hr_result* result)
     result->flags = region->flags | (region->n_races > region->ring_cap ? HR_FLAG_TRUNCATED : 0u);
 }
 
-uint64_t magic(uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; }
-
 }  // namespace
 
 extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n, uint64_t* d_shadow,
@@ -96,6 +94,7 @@ extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n
                                             hr_stream_t stream)
 {
     if ((n > 0 && !d_trace) || !d_shadow || !d_result || (race_cap > 0 && !d_races)) return HR_ERR_INVALID;
+    if (((uintptr_t)d_trace & 15u) != 0) return HR_ERR_INVALID;
     if (n_words == 0 || n_words > (1ull << 32) || block_dim == 0 || warp_size == 0 || warp_size > 32 ||
         n >= (1ull << 40))
         return HR_ERR_INVALID;
@@ -113,7 +112,7 @@ extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n
     w.ctl = (hr_ctl*)(base + OFF_CTL);
     w.max_waves = HR_NOALLOC_MAX_WAVES;
     w.max_intervals = HR_MAX_INTERVALS;
-    hr_geom g{block_dim, warp_size, magic(block_dim), magic(warp_size)};
+    const hr_geom g = hr_make_geom(block_dim, warp_size);
     hr_noalloc_begin<<<1, 1, 0, s>>>(region, (unsigned long long*)d_shadow, n_words, d_races, race_cap, g);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && n > 0)
