@@ -109,6 +109,52 @@ def cpu_oracle_rate(trace, info, n_acc, max_records=None):
     return acc / dt, dt, acc
 
 
+def instrumented_slowdown(dev, reps=20):
+    """Time each synthetic kernel without and with inline hr_access() calls
+    (1,048,576 threads, block 256; clean variants).  Returns per-kernel ms and
+    the slowdown ratio; the instrumented runs check a fresh kernel each rep."""
+    import torch
+    from paper_2401_04701_gb300 import hirace
+    hirace.load_workloads()
+    n, n_bins = 1 << 20, 4096
+    d_in = torch.rand(n, device=dev)
+    d_out = torch.zeros(n, device=dev)
+    keys = torch.randint(0, n_bins, (n,), device=dev, dtype=torch.int32)
+    bins = torch.zeros(n_bins, dtype=torch.int32, device=dev)
+    red = torch.rand(n, device=dev)
+    jobs = {
+        "stencil": (2 * n, lambda v: hirace.run_stencil(v, d_in, d_out)),
+        "histogram": (n_bins, lambda v: hirace.run_histogram(v, keys, bins)),
+        "reduction": (n, lambda v: hirace.run_reduce(v, red)),
+    }
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for name, (n_words, fn) in jobs.items():
+        with hirace.Checker([dict(n_words=n_words, block_dim=256)], report_capacity=1 << 16) as ck:
+            times = {}
+            for mode in ("plain", "instrumented"):
+                total = 0.0
+                for r in range(reps + 2):
+                    view = ck.device_view(0) if mode == "instrumented" else None
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    fn(view)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    if r >= 2:
+                        total += a.elapsed_time(b)
+                    if mode == "instrumented":
+                        ck.sync(0)
+                times[mode] = total / reps
+            _, status, n_total, _ = ck.report(0)
+        out[name] = {"plain_ms": times["plain"], "instrumented_ms": times["instrumented"],
+                     "slowdown": times["instrumented"] / times["plain"], "races": n_total,
+                     "status": hirace.STATUS[status]}
+    gm = float(np.exp(np.mean([np.log(v["slowdown"]) for v in out.values()])))
+    return {"kernels": out, "slowdown_geomean": gm, "threads": n, "block": 256}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -241,6 +287,8 @@ def run_gpu(args, rank, world, local_rank):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if not args.no_instrumented:
+        line["instrumented_slowdown"] = instrumented_slowdown(dev)
     print(json.dumps(line), flush=True)
     ck.close()
 
@@ -253,6 +301,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-instrumented", action="store_true")
     ap.add_argument("--blocks", type=int, default=1024,
                     help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()

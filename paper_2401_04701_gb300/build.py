@@ -18,9 +18,11 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhirace.so")
+WORKLOADS_LIB = os.path.join(PKG, "libhirace_workloads.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["hr_kernels.cu", "hr_api.cu", "hr_fsm.cpp", "hr_noalloc.cu"]
+WORKLOAD_SOURCES = ["hr_workloads.cu"]
 
 
 def _nvcc() -> str:
@@ -47,9 +49,9 @@ def _compile(src: str, verbose: bool) -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(WORKLOADS_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(WORKLOADS_LIB))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
            [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
@@ -59,14 +61,17 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [_nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-Xcompiler", "-fPIC"]
-    res = subprocess.run(cmd, capture_output=True, text=True)
-    if res.returncode != 0:
-        raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
-    os.replace(tmp, LIB)
+    every = SOURCES + WORKLOAD_SOURCES
+    with cf.ThreadPoolExecutor(len(every)) as ex:
+        objs = dict(zip(every, ex.map(lambda s: _compile(s, verbose), every)))
+    for lib, srcs in ((LIB, SOURCES), (WORKLOADS_LIB, WORKLOAD_SOURCES)):
+        tmp = lib + ".tmp%d" % os.getpid()
+        cmd = [_nvcc(), "-shared", "-o", tmp] + [objs[s] for s in srcs] + ARCH + \
+              ["-cudart", "static", "-Xcompiler", "-fPIC"]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("link failed:\n%s\n%s" % (res.stdout, res.stderr))
+        os.replace(tmp, lib)
     return LIB
 
 

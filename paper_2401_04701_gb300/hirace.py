@@ -33,6 +33,22 @@ class HrRegionDesc(ctypes.Structure):
                 ("space", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("report_capacity", ctypes.c_uint64)]
 
 
+class HrGeom(ctypes.Structure):
+    _fields_ = [("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32), ("bd_magic", ctypes.c_uint64),
+                ("ws_magic", ctypes.c_uint64), ("bd_shift", ctypes.c_uint32), ("ws_shift", ctypes.c_uint32)]
+
+
+class HrView(ctypes.Structure):
+    """Mirror of hr_view (include/hirace_device.cuh): what an instrumented kernel gets by value."""
+    _fields_ = [("shadow", ctypes.c_void_p), ("ring", ctypes.c_void_p), ("n_races", ctypes.c_void_p),
+                ("error", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("table", ctypes.c_void_p),
+                ("n_words", ctypes.c_uint64), ("ring_cap", ctypes.c_uint64), ("geom", HrGeom),
+                ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32)]
+
+
+assert ctypes.sizeof(HrView) == 104
+
+
 class HiRaceError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -64,6 +80,8 @@ def load_library():
     lib.hr_profile_enable.argtypes = [P, i32]
     lib.hr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.hr_device_view.argtypes = [P, u32, ctypes.POINTER(HrView)]
+    lib.hr_device_view.restype = i32
     lib.hr_status_str.argtypes = [i32]
     lib.hr_status_str.restype = ctypes.c_char_p
     lib.hr_fsm_table.argtypes = [P, ctypes.POINTER(u32)]
@@ -180,6 +198,12 @@ class Checker:
     def reset(self, region: int, stream=None):
         self._check(self._lib.hr_reset(self._ctx, region, _stream_handle(stream)), "hr_reset")
 
+    def device_view(self, region: int) -> HrView:
+        """The by-value view an instrumented kernel needs (kernel ordinal = hr_sync count)."""
+        v = HrView()
+        self._check(self._lib.hr_device_view(self._ctx, region, ctypes.byref(v)), "hr_device_view")
+        return v
+
     def profile(self, on: bool = True):
         self._check(self._lib.hr_profile_enable(self._ctx, int(on)), "hr_profile_enable")
 
@@ -212,3 +236,50 @@ class Checker:
 def race_keys(races) -> set:
     """{(kernel, word, epoch)} of a race array."""
     return {(int(k), int(w), int(e)) for k, w, e in zip(races["kernel"], races["word"], races["epoch"])}
+
+
+# ---------------------------------------------------------------------------
+# Hand-instrumented synthetic kernels (libhirace_workloads.so)
+# ---------------------------------------------------------------------------
+
+_wl = None
+
+
+def load_workloads():
+    """Stencil, histogram and reduction kernels, instrumented with hr_access()."""
+    global _wl
+    if _wl is not None:
+        return _wl
+    if not os.path.exists(_build.WORKLOADS_LIB):
+        raise RuntimeError("libhirace_workloads.so is not built (run __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.WORKLOADS_LIB)
+    P, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int
+    VP = ctypes.POINTER(HrView)
+    lib.hrw_stencil.argtypes = [VP, P, P, u32, u32, u32, P]
+    lib.hrw_histogram.argtypes = [VP, P, u32, P, u32, u32, P]
+    lib.hrw_reduce.argtypes = [VP, P, u32, u32, i32, P]
+    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce):
+        f.restype = i32
+    _wl = lib
+    return lib
+
+
+def run_stencil(view, d_in, d_out, block=256, racy_stride=0, stream=None):
+    rc = load_workloads().hrw_stencil(ctypes.byref(view) if view is not None else None, d_in.data_ptr(),
+                                      d_out.data_ptr(), d_in.numel(), block, racy_stride, _stream_handle(stream))
+    if rc:
+        raise RuntimeError("hrw_stencil failed (%d)" % rc)
+
+
+def run_histogram(view, d_keys, d_bins, block=256, racy_stride=0, stream=None):
+    rc = load_workloads().hrw_histogram(ctypes.byref(view) if view is not None else None, d_keys.data_ptr(),
+                                        d_keys.numel(), d_bins.data_ptr(), block, racy_stride, _stream_handle(stream))
+    if rc:
+        raise RuntimeError("hrw_histogram failed (%d)" % rc)
+
+
+def run_reduce(view, d_data, block=256, drop_level=-1, stream=None):
+    rc = load_workloads().hrw_reduce(ctypes.byref(view) if view is not None else None, d_data.data_ptr(),
+                                     d_data.numel(), block, drop_level, _stream_handle(stream))
+    if rc:
+        raise RuntimeError("hrw_reduce failed (%d)" % rc)

@@ -296,3 +296,88 @@ def gen_global_mix(seed: int, inject: bool = True, n_blocks: int = 1024, block_d
     info = dict(n_words=n_words, block_dim=block_dim, n_threads=n_blocks * block_dim,
                 injected=injected)
     return rec, info
+
+
+# --------------------------------------------------------------------------
+# Access programs of the hand-instrumented kernels (same accesses, as traces)
+# --------------------------------------------------------------------------
+
+def _pack(word, tid, bc, op, step):
+    """Records from per-access columns, ordered by (bc, step, tid)."""
+    word, tid, bc, op, step = (np.asarray(x, dtype=np.int64) for x in (word, tid, bc, op, step))
+    order = np.lexsort((tid, step, bc))
+    rec = np.zeros(len(order), RECORD)
+    rec["word"] = word[order]
+    rec["tid"] = tid[order]
+    rec["bc"] = bc[order]
+    rec["op"] = op[order]
+    return rec
+
+
+def stencil_program(n: int, racy_stride: int = 0) -> np.ndarray:
+    """Thread i reads in[i], in[i-1], in[i+1] (words i-1..i+1) and writes out[i]
+    (word n+i); with racy_stride, threads i % racy_stride == 0 also write in[i]."""
+    i = np.arange(n, dtype=np.int64)
+    cols = [(i, i, np.zeros(n), np.full(n, OP_R), np.zeros(n))]
+    m = i > 0
+    cols.append((i[m] - 1, i[m], np.zeros(m.sum()), np.full(m.sum(), OP_R), np.ones(m.sum())))
+    m = i + 1 < n
+    cols.append((i[m] + 1, i[m], np.zeros(m.sum()), np.full(m.sum(), OP_R), np.full(m.sum(), 2)))
+    cols.append((n + i, i, np.zeros(n), np.full(n, OP_W), np.full(n, 3)))
+    if racy_stride:
+        m = i % racy_stride == 0
+        cols.append((i[m], i[m], np.zeros(m.sum()), np.full(m.sum(), OP_W), np.full(m.sum(), 4)))
+    return _pack(*(np.concatenate([c[j] for c in cols]) for j in range(5)))
+
+
+def histogram_program(keys: np.ndarray, racy_stride: int = 0) -> np.ndarray:
+    """Thread i does atomicAdd(bins[keys[i]]); with racy_stride, threads
+    i % racy_stride == 0 do a plain read then write of that bin instead."""
+    keys = np.asarray(keys, dtype=np.int64)
+    n = len(keys)
+    i = np.arange(n, dtype=np.int64)
+    racy = (i % racy_stride == 0) if racy_stride else np.zeros(n, bool)
+    a = ~racy
+    cols = [(keys[a], i[a], np.zeros(a.sum()), np.full(a.sum(), OP_A), np.zeros(a.sum())),
+            (keys[racy], i[racy], np.zeros(racy.sum()), np.full(racy.sum(), OP_R), np.zeros(racy.sum())),
+            (keys[racy], i[racy], np.zeros(racy.sum()), np.full(racy.sum(), OP_W), np.ones(racy.sum()))]
+    return _pack(*(np.concatenate([c[j] for c in cols]) for j in range(5)))
+
+
+def reduce_program(n: int, block: int, drop_level: int = -1) -> np.ndarray:
+    """Per block b, a tree reduction over data[2*block*b ...]: at level L (stride
+    s = block >> L) thread t < s reads t and t+s and writes t, then a barrier
+    (removed after level drop_level)."""
+    grid = -(-n // (2 * block))
+    parts = []
+    bc = 0
+    level = 0
+    s = block
+    b = np.arange(grid, dtype=np.int64).reshape(-1, 1)
+    while s > 0:
+        t = np.arange(block, dtype=np.int64).reshape(1, -1)
+        base = 2 * block * b
+        ok = (t < s) & (base + t + s < n)
+        tid = np.broadcast_to(b * block + t, ok.shape)[ok]
+        w0 = np.broadcast_to(base + t, ok.shape)[ok]
+        w1 = np.broadcast_to(base + t + s, ok.shape)[ok]
+        k = len(tid)
+        step = 3 * level
+        parts.append((w0, tid, np.full(k, bc), np.full(k, OP_R), np.full(k, step)))
+        parts.append((w1, tid, np.full(k, bc), np.full(k, OP_R), np.full(k, step + 1)))
+        parts.append((w0, tid, np.full(k, bc), np.full(k, OP_W), np.full(k, step + 2)))
+        if level != drop_level:
+            bc += 1
+            every = (b * block + t).ravel()
+            parts.append((np.zeros(len(every)), every, np.full(len(every), bc),
+                          np.full(len(every), OP_SYNCTHREADS), np.full(len(every), step + 2.5)))
+        s >>= 1
+        level += 1
+    word, tid, bcs, op, step = (np.concatenate([p[j] for p in parts]) for j in range(5))
+    order = np.lexsort((tid, step, bcs))
+    rec = np.zeros(len(order), RECORD)
+    rec["word"] = word[order].astype(np.int64)
+    rec["tid"] = tid[order]
+    rec["bc"] = bcs[order]
+    rec["op"] = op[order]
+    return rec
