@@ -155,6 +155,53 @@ def instrumented_slowdown(dev, reps=20):
     return {"kernels": out, "slowdown_geomean": gm, "threads": n, "block": 256}
 
 
+def other_workloads(dev, reps=5):
+    """The tree-reduction workload (1 block, 1,029,952+ records) and the power-law
+    push workload (2^22 vertices, 4 sweeps, 536,870,912 records): accesses/s of the
+    warp-aggregated and the plain kernel, FSM-kernel time from the library's events."""
+    import torch
+    from paper_2401_04701_gb300 import hirace, tracegen as tg
+    out = {}
+    cases = [("tree_reduction_shared_1x256", lambda: tg.gen_tree_reduction(tg.seed_for(1), inject=True)),
+             ("powerlaw_push_2^22v_16deg_4sweeps", lambda: tg.gen_powerlaw_push(tg.seed_for(3)))]
+    for name, make in cases:
+        trace, info = make()
+        n_acc = int(np.count_nonzero(trace["op"] <= 2))
+        d = torch.from_numpy(trace.view(np.uint8)).to(dev)
+        res = {"records": len(trace), "accesses": n_acc}
+        with hirace.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])],
+                            report_capacity=1 << 22) as ck:
+            for agg in (True, False):
+                ck.reset(0)
+                ck.check_trace(0, d, aggregate=agg)
+                ck.report(0)
+                ck.profile(True)
+                ck.profile_read()
+                start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                tot = 0.0
+                for _ in range(reps):
+                    ck.reset(0)
+                    torch.cuda.synchronize()
+                    start.record()
+                    ck.check_trace(0, d, aggregate=agg)
+                    stop.record()
+                    torch.cuda.synchronize()
+                    tot += start.elapsed_time(stop)
+                prof = ck.profile_read()
+                ck.profile(False)
+                races, status, n_total, _ = ck.report(0)
+                cnt = ck.counters(0)
+                key = "aggregated" if agg else "plain"
+                res[key] = {"accesses_per_s": n_acc * reps / (tot / 1e3), "ms_per_check": tot / reps,
+                            "kernel_ms": prof["check_ms"] / max(1, prof["calls"]), "races": n_total,
+                            "status": hirace.STATUS[status], "cas_last_check": int(cnt["cas"]),
+                            "merged_lanes_last_check": int(cnt["merged"])}
+        out[name] = res
+        del d
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -289,6 +336,8 @@ def run_gpu(args, rank, world, local_rank):
         line["cpu_baseline"] = cpu
     if not args.no_instrumented:
         line["instrumented_slowdown"] = instrumented_slowdown(dev)
+    if args.all_workloads:
+        line["other_workloads"] = other_workloads(dev)
     print(json.dumps(line), flush=True)
     ck.close()
 
@@ -302,6 +351,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-instrumented", action="store_true")
+    ap.add_argument("--all-workloads", action="store_true",
+                    help="also time the tree-reduction and power-law workloads (adds ~2 min)")
     ap.add_argument("--blocks", type=int, default=1024,
                     help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()

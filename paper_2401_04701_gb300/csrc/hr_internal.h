@@ -80,7 +80,17 @@ constexpr int HR_CONSUMERS = 8;                          // consumer warps per C
 constexpr int HR_THREADS = (HR_CONSUMERS + 1) * 32;      // + one producer warp
 constexpr int HR_RPL = 4;                                // records per consumer lane per tile
 constexpr int HR_TILE = HR_CONSUMERS * 32 * HR_RPL;      // records per tile (one wave per tile)
-constexpr int HR_RING = 2;                               // tiles in flight in shared memory
+#ifndef HR_RING_DEPTH
+#define HR_RING_DEPTH 2
+#endif
+#ifndef HR_BATCH
+#define HR_BATCH 1
+#endif
+#ifndef HR_MIN_CTAS
+#define HR_MIN_CTAS 3
+#endif
+constexpr int HR_RING = HR_RING_DEPTH;                   // tiles in flight in shared memory
+constexpr unsigned HR_TICKET_BATCH = HR_BATCH;           // tiles a producer claims per ticket
 constexpr unsigned HR_CLEAR_WORDS = 1u << 16;  // shadow words per clear item
 constexpr unsigned HR_MAX_INTERVALS = 1u << 16;
 constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;

@@ -32,15 +32,6 @@ __device__ __forceinline__ unsigned long long key_at(const hr_record* t, unsigne
     return (__ldg(p) & HR_KEY_MASK) + kb;
 }
 
-__device__ __forceinline__ uint4 ld_stream(const hr_record* p)
-{
-    uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
-}
-
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p)
 {
     unsigned v;
@@ -242,7 +233,7 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
 // their records sit in registers, and apply them to the shadow.  A tile of
 // wave w may only touch the shadow once every tile of the previous stage is
 // done (per-warp completion counts with release/acquire); while it waits, the
-// warp already loads its shadow words and then validates them with the CAS.
+// warp prefetches its shadow lines into L2.
 
 struct TileInfo {
     unsigned long long rb, re, key;  // record range and wave key of the tile
@@ -353,9 +344,15 @@ __device__ __noinline__ unsigned long long fold_group(unsigned long long o, unsi
                                                          const hr_geom& g, const unsigned char* table,
                                                          unsigned* raced, unsigned* who)
 {
+    unsigned last_tid = ~0u, last_op = ~0u;
     while (grp) {
         const unsigned l = __ffs(grp) - 1;
         grp &= grp - 1;
+        // the summary depends on the set of accesses: a repeat of the access
+        // just applied (same thread, same op, same wave) changes nothing
+        if (acc[l].tid == last_tid && acc[l].op == last_op) continue;
+        last_tid = acc[l].tid;
+        last_op = acc[l].op;
         unsigned r = 0;
         o = hr_fsm_step(o, acc[l].tid, acc[l].op, bc, wc, ktag, g, table, &r);
         if (r && !*raced) {
@@ -405,6 +402,8 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
     unsigned s = 0, s_begin = 0, s_end = 0, type = 0, prev_need = 0;
     unsigned long long w_start = 0, w_end = 0, key = 0;
     bool have = false;
+    unsigned pend = 0, pend_end = 0, polls = 0;
+    bool skip = *(volatile unsigned*)&region->error != 0;
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (it >= HR_RING &&
@@ -413,8 +412,13 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
             mbar_arrive(&s_full[b]);
             return;
         }
-        const unsigned t = atomicAdd(&w.ctl->ticket, 1u);
-        if (t >= total || *(volatile unsigned*)&w.ctl->abort) {
+        if (pend == pend_end) {  // claim the next batch of tiles
+            pend = atomicAdd(&w.ctl->ticket, HR_TICKET_BATCH);
+            pend_end = min(pend + HR_TICKET_BATCH, total);
+            if (++polls % 8 == 0) skip = *(volatile unsigned*)&region->error != 0;
+        }
+        const unsigned t = pend++;
+        if (t >= total || (polls % 8 == 0 && *(volatile unsigned*)&w.ctl->abort)) {
             s_info[b].valid = 0;
             mbar_arrive(&s_full[b]);
             return;
@@ -438,7 +442,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
         info.type = type;
         info.item = t - s_begin;
         info.prev_need = prev_need;
-        info.skip = *(volatile unsigned*)&region->error != 0;
+        info.skip = skip;
         info.key = key;
         info.rb = w_start + (unsigned long long)info.item * HR_TILE;
         info.re = min(info.rb + HR_TILE, w_end);
@@ -454,7 +458,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
 }
 
 template <bool AGG>
-__global__ void __launch_bounds__(HR_THREADS, 3) hr_check_kernel(hr_region_dev* __restrict__ region, hr_work w,
+__global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_region_dev* __restrict__ region, hr_work w,
                                                                  const hr_record* __restrict__ trace,
                                                                  const unsigned char* __restrict__ gtable,
                                                                  unsigned long long kb)
@@ -570,12 +574,29 @@ __global__ void __launch_bounds__(HR_THREADS, 3) hr_check_kernel(hr_region_dev* 
                 grp[k] = 1u << lane;
                 if (AGG) {
                     const unsigned am = __ballot_sync(0xffffffffu, a);
-                    // cheap screen: only run the match when a neighbour lane repeats the word
-                    const unsigned up = __shfl_up_sync(0xffffffffu, v.x, 1);
-                    const bool adj = a && lane > 0 && ((am >> (lane - 1)) & 1u) && up == v.x;
-                    if (__any_sync(0xffffffffu, adj)) {
+                    const unsigned w1 = __shfl_up_sync(0xffffffffu, v.x, 1);
+                    const unsigned w2 = __shfl_up_sync(0xffffffffu, v.x, 2);
+                    const unsigned t1 = __shfl_up_sync(0xffffffffu, v.y, 1);
+                    const unsigned t2 = __shfl_up_sync(0xffffffffu, v.y, 2);
+                    const unsigned o1 = __shfl_up_sync(0xffffffffu, op, 1);
+                    const unsigned o2 = __shfl_up_sync(0xffffffffu, op, 2);
+                    const bool a1 = lane >= 1 && ((am >> (lane - 1)) & 1u);
+                    const bool a2 = lane >= 2 && ((am >> (lane - 2)) & 1u);
+                    // an exact repeat (same word, thread, op, wave) of an access a lower
+                    // lane applies adds nothing to the summary: drop it
+                    const bool dup = a && ((a1 && w1 == v.x && t1 == v.y && o1 == op) ||
+                                           (a2 && w2 == v.x && t2 == v.y && o2 == op));
+                    if (dup) {
+                        a = false;
+                        act[k] = false;
+                        c_merged++;
+                    }
+                    // other same-word lanes nearby: group them and let the lowest lane fold
+                    const bool near = a && ((a1 && w1 == v.x) || (a2 && w2 == v.x));
+                    if (__any_sync(0xffffffffu, near)) {
                         my_acc[k * 32 + lane] = Acc{v.y, op};
-                        const unsigned m = __match_any_sync(0xffffffffu, a ? v.x : 0xFFFFFFFFu) & am;
+                        const unsigned am2 = __ballot_sync(0xffffffffu, a);
+                        const unsigned m = __match_any_sync(0xffffffffu, a ? v.x : 0xFFFFFFFFu) & am2;
                         if (a) {
                             grp[k] = m;
                             if ((unsigned)(__ffs(m) - 1) != lane) {
@@ -590,6 +611,19 @@ __global__ void __launch_bounds__(HR_THREADS, 3) hr_check_kernel(hr_region_dev* 
             if (err) hr_set_error(&region->error, err);
             __syncwarp();
 
+            if (!ready) {
+                // the previous stage is still running: pull this tile's shadow lines
+                // into L2 while waiting for it, then load them fresh
+#pragma unroll
+                for (int k = 0; k < HR_RPL; ++k)
+                    if (act[k]) asm volatile("prefetch.global.L2 [%0];" ::"l"(shadow + word[k]));
+                bool ok = true;
+                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                __syncwarp();
+                if (!ok) break;
+                known = (int)s - 1;
+            }
             unsigned long long o[HR_RPL], nv[HR_RPL];
             unsigned raced[HR_RPL], who[HR_RPL];
 #pragma unroll
@@ -610,20 +644,10 @@ __global__ void __launch_bounds__(HR_THREADS, 3) hr_check_kernel(hr_region_dev* 
                     }
                 }
             }
-            bool force = false;
-            if (!ready) {  // the loads above ran ahead of the previous stage: validate them by CAS
-                bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
-                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                __syncwarp();
-                if (!ok) break;
-                known = (int)s - 1;
-                force = true;
-            }
             bool need[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
-                need[k] = act[k] && (force || nv[k] != o[k]);
+                need[k] = act[k] && nv[k] != o[k];
                 if (need[k]) nv[k] = atomicCAS(shadow + word[k], o[k], nv[k]);  // nv now holds the value seen
             }
 #pragma unroll

@@ -63,10 +63,11 @@ def load_library():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
+    path = os.environ.get("HIRACE_LIB", _build.LIB)   # a custom build of the same C-ABI
+    if not os.path.exists(path):
         raise RuntimeError("libhirace.so is not built (run __graft_entry__.build()); "
                            "the checker has no CPU fallback")
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
     P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
     lib.hr_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64, P]
     lib.hr_check_trace.argtypes = [P, u32, P, u64, P]

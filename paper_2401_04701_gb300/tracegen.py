@@ -381,3 +381,60 @@ def reduce_program(n: int, block: int, drop_level: int = -1) -> np.ndarray:
     rec["bc"] = bcs[order]
     rec["op"] = op[order]
     return rec
+
+
+# --------------------------------------------------------------------------
+# Workload 3: power-law graph, push-style relaxation
+# --------------------------------------------------------------------------
+
+def gen_powerlaw_push(seed: int, log2_vertices: int = 22, avg_degree: int = 16, sweeps: int = 4,
+                      gamma: float = 2.1, block_dim: int = 256, inject_frac: float = 0.0005,
+                      inject: bool = True):
+    """Push-style relaxation over a Chung-Lu power-law graph.
+
+    Vertex weights are proportional to (i+1)^(-1/(gamma-1)); both endpoints of
+    each of the n*avg_degree edges are drawn with those weights, so in- and
+    out-degrees follow a power law with exponent gamma.  Thread v owns vertex v
+    (block_dim threads per block) and, in each of ``sweeps`` kernel launches,
+    visits its out-edges in CSR order: an atomic load of dist[v] (op A, flag
+    atomic-load) then an atomicMin of dist[u] (op A).  There are no barriers,
+    so each launch is one wave; a thread's records are contiguous (the order
+    a per-thread trace buffer produces).  Injection turns ``inject_frac`` of
+    the atomicMins into plain writes.
+
+    Returns (trace, info) with info = dict(n_words, block_dim, n_threads,
+    injected (indices of the injected records), edges).
+    """
+    rng = np.random.default_rng(seed)
+    n = 1 << log2_vertices
+    m = n * avg_degree
+    w = (np.arange(1, n + 1, dtype=np.float64)) ** (-1.0 / (gamma - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    src = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    dst = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    np.minimum(src, n - 1, out=src)
+    np.minimum(dst, n - 1, out=dst)
+    order = np.argsort(src, kind="stable")
+    src = src[order].astype(np.uint32)
+    dst = dst[order].astype(np.uint32)
+    del order
+    per = 2 * m
+    trace = np.zeros(per * sweeps, RECORD)
+    for k in range(sweeps):
+        part = trace[k * per:(k + 1) * per]
+        part["tid"][0::2] = src
+        part["tid"][1::2] = src
+        part["word"][0::2] = src
+        part["word"][1::2] = dst
+        part["op"] = OP_A
+        part["flags"][0::2] = FLAG_ATOMIC_LOAD
+        part["kernel"] = k
+    injected = np.zeros(0, np.int64)
+    if inject:
+        n_inj = int(inject_frac * m * sweeps)
+        picks = rng.choice(m * sweeps, size=n_inj, replace=False)
+        injected = np.sort((picks // m) * per + 2 * (picks % m) + 1)
+        trace["op"][injected] = OP_W
+    info = dict(n_words=n, block_dim=block_dim, n_threads=n, injected=injected, edges=m)
+    return trace, info
