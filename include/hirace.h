@@ -164,6 +164,35 @@ hr_status hr_check_trace_kbase(hr_ctx* ctx, uint32_t region, const hr_record* d_
 hr_status hr_check_trace_plain(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
                                hr_stream_t stream);
 
+/* One job of a batched check: a trace for one region of the context. */
+typedef struct hr_job {
+    uint32_t region;
+    uint32_t reserved;       /* must be 0 */
+    const hr_record* trace;  /* device pointer, 16-byte aligned, same rules as hr_check_trace */
+    uint64_t n;
+} hr_job;
+
+/*
+ * hr_check_batch - check many traces, each on its own region, in one
+ * persistent launch (the per-job result equals hr_check_trace on that job
+ * alone).  jobs is a host array of n_jobs <= 512 entries naming distinct
+ * regions (HR_ERR_INVALID otherwise).  The jobs' stages are interleaved
+ * wave-major (every job's first wave, then every job's second wave, ...) and
+ * each stage waits only for the previous stage of its own job, so independent
+ * traces fill each other's wave boundaries.  Asynchronous.  The first call
+ * allocates the batch scratch (call hr_batch_reserve first to keep later calls
+ * allocation-free, e.g. inside CUDA-graph capture).
+ */
+hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_jobs, hr_stream_t stream);
+
+/* Calls queued inside a stream capture (CUDA graphs) record no completion
+ * event: synchronise the replay stream before hr_report on those regions
+ * (hr_report then waits for the whole device). */
+
+/* Size the batch scratch for up to max_jobs jobs and max_waves waves per call
+ * (synchronises the device).  Errors: HR_ERR_INVALID, HR_ERR_OOM. */
+hr_status hr_batch_reserve(hr_ctx* ctx, uint32_t max_jobs, uint64_t max_waves);
+
 /*
  * hr_sync - kernel end for a region (Sec. II-B: the end of a kernel orders
  * every access of that kernel before every access of the next one).  Only
@@ -223,7 +252,7 @@ hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uin
  *   d_result  device hr_result, overwritten: races found by this call (may
  *             exceed race_cap), its sticky error, HR_FLAG_* flags
  * The wave pre-pass scratch is a file-scope device array of
- * HR_NOALLOC_SCRATCH_BYTES (451 KiB) inside the library; every GPU that loads
+ * HR_NOALLOC_SCRATCH_BYTES (611 KiB) inside the library; every GPU that loads
  * the library holds it until the process exits.  Its limit: at most
  * HR_NOALLOC_MAX_WAVES waves (distinct (kernel, bc, wc) keys) per call; a
  * longer trace is rejected on the device with d_result->error ==
@@ -238,7 +267,7 @@ hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uin
  * d_result->error.
  */
 #define HR_NOALLOC_MAX_WAVES 4096u
-#define HR_NOALLOC_SCRATCH_BYTES 461824u
+#define HR_NOALLOC_SCRATCH_BYTES 625664u
 
 typedef struct hr_result {
     uint64_t n_races;

@@ -20,7 +20,23 @@ struct RegionHost {
     hr_work work{};
     unsigned kernel = 0;                  // kernel ordinal seen by device views
     cudaEvent_t done = nullptr;           // recorded after every call on the region
+    bool captured = false;                // work was queued inside a stream capture
 };
+
+// Record the region's completion event, unless the stream is being captured
+// into a CUDA graph (an event recorded there is only a graph edge); then
+// hr_report falls back to a device-wide synchronisation.
+cudaError_t mark_done(RegionHost& r, cudaStream_t s)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) {
+        r.captured = true;
+        return cudaSuccess;
+    }
+    return cudaEventRecord(r.done, s);
+}
 
 hr_status cuda_status(cudaError_t e)
 {
@@ -50,6 +66,10 @@ struct hr_ctx {
     hr_region_dev* d_regions = nullptr;
     unsigned char* d_table = nullptr;
     bool profile = false;
+    void* batch_mem = nullptr;         // scratch of hr_check_batch (allocated on first use)
+    hr_work batch{};
+    unsigned batch_jobs = 0;
+    unsigned long long batch_waves = 0;
     std::vector<ProfiledCall> calls;   // profiled calls not read yet
     std::vector<ProfiledCall> spare;   // event triples to reuse
 };
@@ -83,6 +103,7 @@ static void free_ctx(hr_ctx* c)
             cudaEventDestroy(p.mid);
             cudaEventDestroy(p.end);
         }
+    cudaFree(c->batch_mem);
     cudaFree(c->d_regions);
     cudaFree(c->d_table);
     delete c;
@@ -122,26 +143,11 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         r.d = c->d_regions + i;
         e = cudaMalloc(&r.shadow, r.desc.n_words * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
-        // scratch of one trace check: interval counts, wave table, stages, control block
-        const size_t b_counts = HR_MAX_INTERVALS * sizeof(unsigned);
-        const size_t b_start = (size_t)(max_waves + 1) * sizeof(unsigned long long);
-        const size_t b_key = (size_t)max_waves * sizeof(unsigned long long);
-        const size_t b_stages = (size_t)(2 * max_waves + 1) * sizeof(hr_stage);
-        const size_t total = b_counts + b_start + b_key + b_stages + sizeof(hr_ctl) + 256;
+        // scratch of one trace check: job table, interval counts, wave table, stages, control block
+        const size_t total = hr_work_bytes(1, HR_MAX_INTERVALS, max_waves);
         if (e == cudaSuccess) e = cudaMalloc(&r.work_mem, total);
         if (e == cudaSuccess) {
-            char* p = (char*)r.work_mem;
-            r.work.counts = (unsigned*)p;
-            p += b_counts;
-            r.work.wave_start = (unsigned long long*)p;
-            p += b_start;
-            r.work.wave_key = (unsigned long long*)p;
-            p += b_key;
-            r.work.stages = (hr_stage*)p;
-            p += b_stages;
-            r.work.ctl = (hr_ctl*)p;
-            r.work.max_waves = max_waves;
-            r.work.max_intervals = HR_MAX_INTERVALS;
+            r.work = hr_work_at(r.work_mem, 1, HR_MAX_INTERVALS, max_waves);
             e = cudaMemsetAsync(r.work_mem, 0, total, s);
         }
         if (e == cudaSuccess) e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
@@ -174,20 +180,27 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     if (((uintptr_t)d_trace & 15u) != 0) return HR_ERR_INVALID;  // records are copied in 16-byte units
     if (n >= (1ull << 40)) return HR_ERR_INVALID;
     if (n == 0) return HR_OK;
+    (void)cudaGetLastError();  // report only errors of this call's launches
     RegionHost& r = ctx->regions[region];
     cudaStream_t s = (cudaStream_t)stream;
+    hr_jobd job{};
+    job.trace = d_trace;
+    job.n = n;
+    job.kb = (unsigned long long)kernel_base << 32;
+    job.region = region;
+    job.int_begin = 0;
+    hr_plan_intervals(n, HR_MAX_INTERVALS, &job.G, &job.n_int);
     ProfiledCall pc{};
     if (ctx->profile) pc = take_events(ctx);
-    cudaEvent_t mid = ctx->profile ? pc.mid : nullptr;
     if (ctx->profile) cudaEventRecord(pc.begin, s);
-    cudaError_t e = hr_launch_check(r.d, r.work, d_trace, n, kernel_base, ctx->d_table, aggregate,
-                                    hr_check_grid_size(aggregate), s, mid);
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, r.work, &job, 1, ctx->d_table, aggregate,
+                                   hr_check_grid_size(aggregate), s, ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
         pc.launches = HR_LAUNCHES_PER_CHECK;
         ctx->calls.push_back(pc);
     }
-    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    if (e == cudaSuccess) e = mark_done(r, s);
     return cuda_status(e);
 }
 
@@ -209,18 +222,95 @@ extern "C" hr_status hr_check_trace_plain(hr_ctx* ctx, uint32_t region, const hr
     return check_common(ctx, region, d_trace, n, 0, stream, false);
 }
 
+extern "C" hr_status hr_batch_reserve(hr_ctx* ctx, uint32_t max_jobs, uint64_t max_waves)
+{
+    if (!ctx || max_jobs == 0 || max_jobs > HR_MAX_BATCH || max_waves == 0 || max_waves > (1ull << 24))
+        return HR_ERR_INVALID;
+    if (ctx->batch_mem && ctx->batch_jobs >= max_jobs && ctx->batch_waves >= max_waves) return HR_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && ctx->batch_mem) e = cudaFree(ctx->batch_mem);
+    ctx->batch_mem = nullptr;
+    const unsigned mj = max_jobs > ctx->batch_jobs ? max_jobs : ctx->batch_jobs;
+    const unsigned mw = (unsigned)(max_waves > ctx->batch_waves ? max_waves : ctx->batch_waves);
+    const size_t bytes = hr_work_bytes(mj, HR_BATCH_INTERVALS, mw);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->batch_mem, bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->batch_mem, 0, bytes);
+    if (e != cudaSuccess) {
+        ctx->batch_mem = nullptr;
+        ctx->batch_jobs = 0;
+        ctx->batch_waves = 0;
+        return cuda_status(e);
+    }
+    ctx->batch = hr_work_at(ctx->batch_mem, mj, HR_BATCH_INTERVALS, mw);
+    ctx->batch_jobs = mj;
+    ctx->batch_waves = mw;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_jobs, hr_stream_t stream)
+{
+    if (!ctx || (n_jobs > 0 && !jobs)) return HR_ERR_INVALID;
+    std::vector<hr_jobd> js;
+    std::vector<char> seen(ctx->regions.size(), 0);
+    for (uint32_t i = 0; i < n_jobs; ++i) {
+        const hr_job& j = jobs[i];
+        if (!valid_region(ctx, j.region) || j.reserved != 0 || (j.n > 0 && !j.trace) || j.n >= (1ull << 40) ||
+            ((uintptr_t)j.trace & 15u) != 0)
+            return HR_ERR_INVALID;
+        if (seen[j.region]) return HR_ERR_INVALID;  // one job per region
+        seen[j.region] = 1;
+        if (j.n == 0) continue;
+        hr_jobd d{};
+        d.trace = j.trace;
+        d.n = j.n;
+        d.region = j.region;
+        js.push_back(d);
+    }
+    if (js.empty()) return HR_OK;
+    if (js.size() > HR_MAX_BATCH) return HR_ERR_INVALID;
+    if (!ctx->batch_mem || ctx->batch_jobs < js.size()) {
+        hr_status st = hr_batch_reserve(ctx, (uint32_t)js.size() > ctx->batch_jobs ? (uint32_t)js.size() : ctx->batch_jobs,
+                                        ctx->batch_waves ? ctx->batch_waves : (1ull << 18));
+        if (st != HR_OK) return st;
+    }
+    // split the pre-pass interval budget across the jobs
+    const unsigned budget = HR_BATCH_INTERVALS / (unsigned)js.size();
+    unsigned at = 0;
+    for (auto& d : js) {
+        hr_plan_intervals(d.n, budget, &d.G, &d.n_int);
+        d.int_begin = at;
+        at += d.n_int;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();  // report only errors of this call's launches
+    ProfiledCall pc{};
+    if (ctx->profile) pc = take_events(ctx);
+    if (ctx->profile) cudaEventRecord(pc.begin, s);
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, ctx->batch, js.data(), (unsigned)js.size(), ctx->d_table, true,
+                                   hr_check_grid_size(true), s, ctx->profile ? pc.mid : nullptr);
+    if (ctx->profile) {
+        cudaEventRecord(pc.end, s);
+        pc.launches = HR_LAUNCHES_PER_CHECK;
+        ctx->calls.push_back(pc);
+    }
+    for (auto& d : js)
+        if (e == cudaSuccess) e = mark_done(ctx->regions[d.region], s);
+    return cuda_status(e);
+}
+
 extern "C" hr_status hr_sync(hr_ctx* ctx, uint32_t region, uint32_t scope, hr_stream_t stream)
 {
     if (!valid_region(ctx, region) || scope != HR_SYNC_KERNEL) return HR_ERR_INVALID;
     RegionHost& r = ctx->regions[region];
     cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();  // report only errors of this call's launches
     // device views (hand instrumentation) tag shadow values with kernel mod 8:
     // when the next kernel starts a new group of 8, clear the shadow
     cudaError_t e = cudaSuccess;
     if (((r.kernel + 1) >> 3) != (r.kernel >> 3))
         e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = hr_launch_sync_kernel(r.d, s);
-    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    if (e == cudaSuccess) e = mark_done(r, s);
     if (e == cudaSuccess) r.kernel++;
     return cuda_status(e);
 }
@@ -228,7 +318,7 @@ extern "C" hr_status hr_sync(hr_ctx* ctx, uint32_t region, uint32_t scope, hr_st
 static hr_status fetch_region(hr_ctx* ctx, uint32_t region, hr_region_dev* out)
 {
     RegionHost& r = ctx->regions[region];
-    cudaError_t e = cudaEventSynchronize(r.done);
+    cudaError_t e = r.captured ? cudaDeviceSynchronize() : cudaEventSynchronize(r.done);
     if (e == cudaSuccess) e = cudaMemcpy(out, r.d, sizeof *out, cudaMemcpyDeviceToHost);
     return cuda_status(e);
 }
@@ -267,8 +357,9 @@ extern "C" hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream)
     if (!valid_region(ctx, region)) return HR_ERR_INVALID;
     RegionHost& r = ctx->regions[region];
     cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();  // report only errors of this call's launches
     cudaError_t e = hr_launch_reset(r.d, r.shadow, r.desc.n_words, s);
-    if (e == cudaSuccess) e = cudaEventRecord(r.done, s);
+    if (e == cudaSuccess) e = mark_done(r, s);
     r.kernel = 0;
     return cuda_status(e);
 }

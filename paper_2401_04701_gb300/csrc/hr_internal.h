@@ -43,38 +43,98 @@ struct hr_region_dev {
     hr_geom geom;
 };
 
-// Work stages of one check: per wave an optional shadow clear (when the kernel
-// tag group changes) followed by the wave's record tiles.
+// One job = one trace checked on one region.  A single-trace check is a batch
+// of one job; a batch interleaves the jobs' stages wave-major.
+struct hr_jobd {
+    const hr_record* trace;
+    unsigned long long n;         // records
+    unsigned long long kb;        // kernel base added to every record's kernel, shifted left by 32
+    unsigned region;
+    unsigned G;                   // records per pre-pass interval
+    unsigned int_begin;           // first global pre-pass interval of this job
+    unsigned n_int;
+    unsigned wave_begin;          // first global wave index (written on the device)
+    unsigned n_waves;             // waves of this job (written on the device)
+};
+
+// Work stages: per wave an optional shadow clear (when the kernel-tag group
+// changes) followed by the wave's record tiles.  A stage waits for `dep`, the
+// previous stage of the same job, to reach `dep_need` per-warp completions.
 enum { HR_STAGE_RECORDS = 0, HR_STAGE_CLEAR = 1 };
+constexpr unsigned HR_NO_DEP = 0xFFFFFFFFu;
 
 struct hr_stage {
-    unsigned int item_begin;  // first global work-item index of the stage
-    unsigned int wave;
-    unsigned int type;
-    unsigned int done;        // items of this stage finished
+    unsigned item_begin;  // first global work-item index of the stage
+    unsigned wave;        // global wave index
+    unsigned type;
+    unsigned done;        // per-warp completions of this stage's items
+    unsigned dep;
+    unsigned dep_need;
+    unsigned job;
+    unsigned pad;
 };
 
 struct hr_ctl {
-    unsigned int ticket;      // next work item
-    unsigned int abort;       // set when a bounded wait expired
-    unsigned int n_waves;
-    unsigned int n_stages;
-    unsigned int total_items;
-    unsigned int n_intervals;
-    unsigned int interval;    // records per pre-pass interval
-    unsigned int pad;
+    unsigned ticket;       // next work item
+    unsigned abort;        // set when a bounded wait expired
+    unsigned n_waves;
+    unsigned n_stages;
+    unsigned total_items;
+    unsigned n_jobs;
+    unsigned n_intervals;
+    unsigned pad;
 };
 
-// Scratch of one region's trace check (device memory).
+// Scratch of one check (device memory): job table, pre-pass counts, wave
+// table, stage list and control block.
 struct hr_work {
-    unsigned int* counts;          // [max_intervals] boundaries per interval, then their offsets
-    unsigned long long* wave_start;  // [max_waves + 1]
-    unsigned long long* wave_key;    // [max_waves]
+    hr_jobd* jobs;                   // [max_jobs]
+    unsigned* counts;                // [max_intervals] boundaries per interval, then their offsets
+    unsigned long long* wave_start;  // [max_waves] first record (index into the job's trace)
+    unsigned long long* wave_end;    // [max_waves] one past the last record
+    unsigned long long* wave_key;    // [max_waves] rebased wave key
     hr_stage* stages;                // [2 * max_waves + 1]
     hr_ctl* ctl;
-    unsigned int max_waves;
-    unsigned int max_intervals;
+    unsigned max_waves;
+    unsigned max_intervals;
+    unsigned max_jobs;
+    unsigned pad;
 };
+
+// bytes of an hr_work scratch block for the given capacities (256-B aligned parts)
+inline size_t hr_work_bytes(unsigned max_jobs, unsigned max_intervals, unsigned max_waves)
+{
+    auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
+    return a(sizeof(hr_ctl)) + a((size_t)max_jobs * sizeof(hr_jobd)) + a((size_t)max_intervals * 4) +
+           3 * a((size_t)max_waves * 8) + a((size_t)(2 * max_waves + 1) * sizeof(hr_stage));
+}
+
+// carve an hr_work out of `mem` (hr_work_bytes(...) bytes, 256-B aligned)
+inline hr_work hr_work_at(void* mem, unsigned max_jobs, unsigned max_intervals, unsigned max_waves)
+{
+    auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
+    char* p = (char*)mem;
+    hr_work w{};
+    w.ctl = (hr_ctl*)p;
+    p += a(sizeof(hr_ctl));
+    w.jobs = (hr_jobd*)p;
+    p += a((size_t)max_jobs * sizeof(hr_jobd));
+    w.counts = (unsigned*)p;
+    p += a((size_t)max_intervals * 4);
+    w.wave_start = (unsigned long long*)p;
+    p += a((size_t)max_waves * 8);
+    w.wave_end = (unsigned long long*)p;
+    p += a((size_t)max_waves * 8);
+    w.wave_key = (unsigned long long*)p;
+    p += a((size_t)max_waves * 8);
+    w.stages = (hr_stage*)p;
+    w.max_waves = max_waves;
+    w.max_intervals = max_intervals;
+    w.max_jobs = max_jobs;
+    return w;
+}
+
+constexpr unsigned HR_MAX_BATCH = 512;  // jobs per batched launch
 
 constexpr int HR_CONSUMERS = 8;                          // consumer warps per CTA
 constexpr int HR_THREADS = (HR_CONSUMERS + 1) * 32;      // + one producer warp
@@ -92,15 +152,20 @@ constexpr int HR_TILE = HR_CONSUMERS * 32 * HR_RPL;      // records per tile (on
 constexpr int HR_RING = HR_RING_DEPTH;                   // tiles in flight in shared memory
 constexpr unsigned HR_TICKET_BATCH = HR_BATCH;           // tiles a producer claims per ticket
 constexpr unsigned HR_CLEAR_WORDS = 1u << 16;  // shadow words per clear item
-constexpr unsigned HR_MAX_INTERVALS = 1u << 16;
+constexpr unsigned HR_MAX_INTERVALS = 1u << 16;      // pre-pass intervals of a single-trace check
+constexpr unsigned HR_BATCH_INTERVALS = 1u << 18;    // pre-pass intervals of a batch
 constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;
 
 // kernel launch helpers (hr_kernels.cu)
-cudaError_t hr_launch_check(hr_region_dev* d_region, const hr_work& w, const hr_record* trace,
-                            unsigned long long n, unsigned kernel_base, const unsigned char* d_table,
-                            bool aggregate, int grid, cudaStream_t stream, cudaEvent_t before_check);
-constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
+// Check n_jobs jobs (1..HR_MAX_BATCH) on the regions of d_regions with the
+// scratch w.  Jobs must name distinct regions and hold n > 0 records.
+cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_jobd* jobs, unsigned n_jobs,
+                           const unsigned char* d_table, bool aggregate, int grid, cudaStream_t stream,
+                           cudaEvent_t before_check);
+// interval size and count for a job of n records when it may use up to budget intervals
+void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int);
 int hr_check_grid_size(bool aggregate);
+constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
 cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long n_words,
                             cudaStream_t stream);

@@ -1,18 +1,23 @@
 // hr_kernels.cu - the trace checker's device code (sm_103a).
 //
-// One hr_check_trace call runs five launches on the caller's stream:
-//   1. hr_scan_intervals   : per interval of G records, count wave boundaries
-//                            (a wave is a run of equal (kernel, bc, wc) keys);
-//                            only intervals whose two end keys differ are read
-//   2. hr_scan_counts      : exclusive scan of the counts (one CTA)
-//   3. hr_write_waves      : wave start offsets and keys
-//   4. hr_build_stages     : work stages: per wave an optional shadow clear
-//                            (kernel-tag group change) then its record tiles
-//   5. hr_check_kernel     : persistent CTAs take work items in ticket order;
-//                            an item waits (bounded) until the previous stage
-//                            is complete, so waves are applied in wave order —
-//                            an order consistent with happens-before (Sec. II-B:
-//                            every ordered pair differs in kernel, bc or wc)
+// A check covers one or more jobs (a job = one trace on one region).  It runs
+// five launches on the caller's stream:
+//   1. hr_scan_intervals : per pre-pass interval of a job's trace, count the
+//                          wave boundaries (a wave is a run of equal
+//                          (kernel, bc, wc) keys); an interval is read only
+//                          when its two end keys differ
+//   2. hr_scan_counts    : exclusive scan of the counts (one CTA): global wave
+//                          numbers, each job's first wave and wave count
+//   3. hr_write_waves    : wave start offsets and keys
+//   4. hr_build_stages   : work stages per wave, an optional shadow clear
+//                          (kernel-tag group change) then the record tiles;
+//                          several jobs are interleaved wave-major
+//   5. hr_check_kernel   : persistent CTAs take work items in ticket order; a
+//                          stage waits (bounded) for the previous stage of the
+//                          same job, so every region sees its waves in wave
+//                          order: an order consistent with happens-before
+//                          (Sec. II-B: every ordered pair differs in kernel,
+//                          bc or wc)
 // Inside a wave every cross-thread pair is unordered, so any order of its
 // records is a valid execution order; each record is applied with the FSM step
 // of Algorithm 1 (hr_fsm_step) and a 64-bit atomicCAS on its shadow word.
@@ -23,6 +28,12 @@
 namespace {
 
 constexpr unsigned long long HR_WAIT_NS = 4000000000ull;  // bounded wait: 4 s
+
+template <unsigned CAP>
+struct JobParams {
+    unsigned n;
+    hr_jobd job[CAP];
+};
 
 // wave key (kernel, bc, wc) of record i; kb is the caller's kernel base, already shifted by 32
 __device__ __forceinline__ unsigned long long key_at(const hr_record* t, unsigned long long i,
@@ -46,20 +57,41 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
+// job holding global pre-pass interval i (jobs sorted by int_begin)
+template <unsigned CAP>
+__device__ __forceinline__ unsigned job_of_interval(const JobParams<CAP>& P, unsigned i)
+{
+    unsigned lo = 0, hi = P.n;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (P.job[mid].int_begin <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------------ wave discovery
 
-__global__ void hr_scan_intervals(const hr_record* __restrict__ trace, unsigned long long n, unsigned G,
-                                  unsigned n_int, unsigned* __restrict__ counts, hr_region_dev* region,
-                                  unsigned long long kb)
+template <unsigned CAP>
+__global__ void hr_scan_intervals(const JobParams<CAP> P, unsigned total_int, hr_work w,
+                                  hr_region_dev* __restrict__ regions)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned n_warps = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned i = warp; i < n_int; i += n_warps) {
-        const unsigned long long beg = (unsigned long long)i * G;
-        const unsigned long long end = min(n, beg + G);
+    if (blockIdx.x == 0) {
+        for (unsigned j = threadIdx.x; j < P.n; j += blockDim.x) w.jobs[j] = P.job[j];
+        if (threadIdx.x == 0) w.ctl->n_jobs = P.n;
+    }
+    for (unsigned i = warp; i < total_int; i += n_warps) {
+        const unsigned j = job_of_interval(P, i);
+        const hr_jobd& jb = P.job[j];
+        const hr_record* trace = jb.trace;
+        const unsigned long long n = jb.n, kb = jb.kb;
+        const unsigned local = i - jb.int_begin;
+        const unsigned long long beg = (unsigned long long)local * jb.G;
+        const unsigned long long end = min(n, beg + jb.G);
         int need = 0;
-        if (lane == 0) need = (i == 0) || key_at(trace, beg - 1, kb) != key_at(trace, end - 1, kb);
+        if (lane == 0) need = (local == 0) || key_at(trace, beg - 1, kb) != key_at(trace, end - 1, kb);
         need = __shfl_sync(0xffffffffu, need, 0);
         unsigned cnt = 0;
         if (need) {
@@ -77,80 +109,89 @@ __global__ void hr_scan_intervals(const hr_record* __restrict__ trace, unsigned 
                     }
                 }
             }
-            if (bad) hr_set_error(&region->error, HR_ERR_ORDER);
+            if (bad) hr_set_error(&regions[jb.region].error, HR_ERR_ORDER);
             for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         }
-        if (lane == 0) counts[i] = cnt;
+        if (lane == 0) w.counts[i] = cnt;
     }
 }
 
 // block-wide exclusive scan of one value per thread (blockDim.x == 1024)
-__device__ unsigned block_exclusive_scan(unsigned v, unsigned* total)
+__device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long* total)
 {
-    __shared__ unsigned s_warp[32];
+    __shared__ unsigned long long s_warp[32];
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned x = v;
+    unsigned long long x = v;
     for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= (unsigned)o) x += y;
     }
     if (lane == 31) s_warp[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        unsigned s = s_warp[lane];
+        unsigned long long s = s_warp[lane];
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, s, o);
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, s, o);
             if (lane >= (unsigned)o) s += y;
         }
         s_warp[lane] = s;
     }
     __syncthreads();
-    const unsigned before = (wid ? s_warp[wid - 1] : 0u) + x - v;
+    const unsigned long long before = (wid ? s_warp[wid - 1] : 0ull) + x - v;
     *total = s_warp[31];
     __syncthreads();
     return before;
 }
 
-__global__ void __launch_bounds__(1024) hr_scan_counts(unsigned* counts, unsigned n_int, hr_work w,
-                                                       hr_region_dev* region)
+__global__ void __launch_bounds__(1024) hr_scan_counts(hr_work w, unsigned total_int, hr_region_dev* regions)
 {
-    const unsigned per = (n_int + 1023) / 1024;
-    const unsigned b = threadIdx.x * per, e = min(n_int, b + per);
+    const unsigned per = (total_int + 1023) / 1024;
+    const unsigned b = threadIdx.x * per, e = min(total_int, b + per);
     unsigned local = 0;
-    for (unsigned i = b; i < e; ++i) local += counts[i];
-    unsigned total;
-    unsigned run = block_exclusive_scan(local, &total);
+    for (unsigned i = b; i < e; ++i) local += w.counts[i];
+    unsigned long long total;
+    unsigned run = (unsigned)block_exclusive_scan(local, &total);
     for (unsigned i = b; i < e; ++i) {
-        const unsigned c = counts[i];
-        counts[i] = run;
+        const unsigned c = w.counts[i];
+        w.counts[i] = run;
         run += c;
+    }
+    __syncthreads();
+    const unsigned n_jobs = w.ctl->n_jobs;
+    const bool over = total > w.max_waves;
+    for (unsigned j = threadIdx.x; j < n_jobs; j += blockDim.x) {
+        hr_jobd& jb = w.jobs[j];
+        const unsigned first = w.counts[jb.int_begin];
+        const unsigned next = jb.int_begin + jb.n_int < total_int ? w.counts[jb.int_begin + jb.n_int] : (unsigned)total;
+        jb.wave_begin = over ? 0u : first;
+        jb.n_waves = over ? 0u : next - first;
+        if (over) hr_set_error(&regions[jb.region].error, HR_ERR_CAPACITY);
     }
     if (threadIdx.x == 0) {
         w.ctl->ticket = 0;
         w.ctl->abort = 0;
         w.ctl->total_items = 0;
         w.ctl->n_stages = 0;
-        if (total > w.max_waves) {
-            hr_set_error(&region->error, HR_ERR_CAPACITY);
-            total = 0;
-        }
-        w.ctl->n_waves = total;
+        w.ctl->n_waves = over ? 0u : (unsigned)total;
     }
 }
 
-__global__ void hr_write_waves(const hr_record* __restrict__ trace, unsigned long long n, unsigned G,
-                               unsigned n_int, hr_work w, unsigned long long kb)
+template <unsigned CAP>
+__global__ void hr_write_waves(const JobParams<CAP> P, unsigned total_int, hr_work w)
 {
     const unsigned lane = threadIdx.x & 31;
     const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned n_warps = (gridDim.x * blockDim.x) >> 5;
     const unsigned n_waves = w.ctl->n_waves;
-    if (warp == 0 && lane == 0) w.wave_start[n_waves] = n;
     if (n_waves == 0) return;
-    for (unsigned i = warp; i < n_int; i += n_warps) {
-        const unsigned long long beg = (unsigned long long)i * G;
-        const unsigned long long end = min(n, beg + G);
-        const unsigned next = (i + 1 < n_int) ? w.counts[i + 1] : n_waves;
+    for (unsigned i = warp; i < total_int; i += n_warps) {
+        const unsigned j = job_of_interval(P, i);
+        const hr_jobd& jb = P.job[j];
+        const unsigned long long kb = jb.kb;
+        const unsigned local = i - jb.int_begin;
+        const unsigned long long beg = (unsigned long long)local * jb.G;
+        const unsigned long long end = min(jb.n, beg + jb.G);
+        const unsigned next = (i + 1 < total_int) ? w.counts[i + 1] : n_waves;
         unsigned off = w.counts[i];
         if (off == next) continue;  // no boundary in this interval
         for (unsigned long long c = beg; c < end; c += 32) {
@@ -158,8 +199,8 @@ __global__ void hr_write_waves(const hr_record* __restrict__ trace, unsigned lon
             bool is_b = false;
             unsigned long long k = 0;
             if (p < end) {
-                k = key_at(trace, p, kb);
-                is_b = (p == 0) || k != key_at(trace, p - 1, kb);
+                k = key_at(jb.trace, p, kb);
+                is_b = (p == 0) || k != key_at(jb.trace, p - 1, kb);
             }
             const unsigned mask = __ballot_sync(0xffffffffu, is_b);
             if (is_b) {
@@ -174,53 +215,137 @@ __global__ void hr_write_waves(const hr_record* __restrict__ trace, unsigned lon
     }
 }
 
-__global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev* region)
+// stage and item counts of wave L of a job, and whether it starts with a clear
+__device__ __forceinline__ void wave_plan(const hr_work& w, const hr_jobd& jb, const hr_region_dev& rg, unsigned L,
+                                          bool* clear, unsigned* rec_items, unsigned* clr_items)
 {
-    const unsigned n_waves = w.ctl->n_waves;
-    const unsigned per = (n_waves + 1023) / 1024;
-    const unsigned b = threadIdx.x * per, e = min(n_waves, b + per);
-    const unsigned long long n_words = region->n_words;
-    const unsigned clear_items = (unsigned)((n_words + HR_CLEAR_WORDS - 1) / HR_CLEAR_WORDS);
-    const bool used = region->used != 0;
-    const unsigned long long last_key = region->last_key;
-    const bool failed = region->error != 0 || (n_waves > 0 && w.wave_key[0] < last_key);
-    // pass 1: stages and items per thread chunk
-    unsigned my_stages = 0, my_items = 0;
-    for (unsigned i = b; i < e; ++i) {
-        const unsigned long long kern = w.wave_key[i] >> 32;
-        const unsigned long long prev = i ? (w.wave_key[i - 1] >> 32) : (last_key >> 32);
-        const bool clear = (i > 0 || used) && (kern >> 3) != (prev >> 3);
-        const unsigned long long len = w.wave_start[i + 1] - w.wave_start[i];
-        my_stages += 1 + clear;
-        my_items += (unsigned)((len + HR_TILE - 1) / HR_TILE) + (clear ? clear_items : 0);
+    const unsigned g = jb.wave_begin + L;
+    const unsigned long long kern = w.wave_key[g] >> 32;
+    const unsigned long long prev = L ? (w.wave_key[g - 1] >> 32) : (rg.last_key >> 32);
+    *clear = (L > 0 || rg.used) && (kern >> 3) != (prev >> 3);
+    const unsigned long long end = L + 1 < jb.n_waves ? w.wave_start[g + 1] : jb.n;
+    w.wave_end[g] = end;
+    *rec_items = (unsigned)((end - w.wave_start[g] + HR_TILE - 1) / HR_TILE);
+    *clr_items = *clear ? (unsigned)((rg.n_words + HR_CLEAR_WORDS - 1) / HR_CLEAR_WORDS) : 0u;
+}
+
+// One job: stages follow its waves; threads take waves in parallel.
+__device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
+{
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev& rg = regions[jb.region];
+    const unsigned nw = jb.n_waves;
+    const bool failed = rg.error != 0 || (nw > 0 && w.wave_key[jb.wave_begin] < rg.last_key);
+    const unsigned per = (nw + 1023) / 1024;
+    const unsigned b = threadIdx.x * per, e = min(nw, b + per);
+    unsigned long long mine = 0;  // (stages << 32) | items
+    for (unsigned L = b; L < e; ++L) {
+        bool clear;
+        unsigned ri, ci;
+        wave_plan(w, jb, rg, L, &clear, &ri, &ci);
+        mine += ((unsigned long long)(1 + clear) << 32) + ri + ci;
     }
-    unsigned tot_stages, tot_items;
-    unsigned s = block_exclusive_scan(my_stages, &tot_stages);
-    unsigned it = block_exclusive_scan(my_items, &tot_items);
-    for (unsigned i = b; i < e; ++i) {
-        const unsigned long long kern = w.wave_key[i] >> 32;
-        const unsigned long long prev = i ? (w.wave_key[i - 1] >> 32) : (last_key >> 32);
-        const bool clear = (i > 0 || used) && (kern >> 3) != (prev >> 3);
-        const unsigned long long len = w.wave_start[i + 1] - w.wave_start[i];
+    unsigned long long tot;
+    const unsigned long long pre = block_exclusive_scan(mine, &tot);
+    unsigned s = (unsigned)(pre >> 32), it = (unsigned)pre;
+    for (unsigned L = b; L < e; ++L) {
+        bool clear;
+        unsigned ri, ci;
+        wave_plan(w, jb, rg, L, &clear, &ri, &ci);
+        const unsigned g = jb.wave_begin + L;
         if (clear) {
-            w.stages[s] = hr_stage{it, i, HR_STAGE_CLEAR, 0u};
+            w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, s ? s - 1 : HR_NO_DEP, 0u, 0u, 0u};
             s++;
-            it += clear_items;
+            it += ci;
         }
-        w.stages[s] = hr_stage{it, i, HR_STAGE_RECORDS, 0u};
+        w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, s ? s - 1 : HR_NO_DEP, 0u, 0u, 0u};
         s++;
-        it += (unsigned)((len + HR_TILE - 1) / HR_TILE);
+        it += ri;
+    }
+    __syncthreads();
+    // dependency need = items of the previous stage x per-warp completions
+    const unsigned n_st = (unsigned)(tot >> 32);
+    for (unsigned i = threadIdx.x; i < n_st; i += blockDim.x)
+        if (i > 0) w.stages[i].dep_need = (w.stages[i].item_begin - w.stages[i - 1].item_begin) * HR_CONSUMERS;
+    if (threadIdx.x == 0) {
+        w.stages[n_st] = hr_stage{(unsigned)tot, 0u, HR_STAGE_RECORDS, 0u, HR_NO_DEP, 0u, 0u, 0u};
+        if (nw > 0 && w.wave_key[jb.wave_begin] < rg.last_key) hr_set_error(&rg.error, HR_ERR_ORDER);
+        w.ctl->n_stages = n_st;
+        w.ctl->total_items = failed ? 0u : (unsigned)tot;
+        if (!failed && nw > 0) {
+            rg.last_key = w.wave_key[jb.wave_begin + nw - 1];
+            rg.used = 1;
+        }
+    }
+}
+
+// Several jobs: stages interleaved wave-major (every job's wave 0, then every
+// job's wave 1, ...), so jobs fill each other's wave-boundary bubbles.  Thread j
+// owns job j.
+__device__ void stages_many_jobs(hr_work& w, hr_region_dev* regions)
+{
+    const unsigned n_jobs = w.ctl->n_jobs;
+    const unsigned j = threadIdx.x;
+    hr_jobd jb{};
+    bool failed = true;
+    unsigned nw = 0;
+    hr_region_dev* rg = nullptr;
+    if (j < n_jobs) {
+        jb = w.jobs[j];
+        rg = &regions[jb.region];
+        nw = jb.n_waves;
+        failed = rg->error != 0 || (nw > 0 && w.wave_key[jb.wave_begin] < rg->last_key);
+        if (nw > 0 && w.wave_key[jb.wave_begin] < rg->last_key) hr_set_error(&rg->error, HR_ERR_ORDER);
+    }
+    __shared__ unsigned s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    if (j < n_jobs && !failed) atomicMax(&s_max, nw);
+    __syncthreads();
+    const unsigned max_w = s_max;
+    unsigned base_s = 0, base_i = 0, last = HR_NO_DEP, last_items = 0;
+    for (unsigned L = 0; L < max_w; ++L) {
+        const bool has = j < n_jobs && !failed && L < nw;
+        bool clear = false;
+        unsigned ri = 0, ci = 0;
+        if (has) wave_plan(w, jb, *rg, L, &clear, &ri, &ci);
+        const unsigned long long mine = has ? (((unsigned long long)(1 + clear) << 32) + ri + ci) : 0ull;
+        unsigned long long tot;
+        const unsigned long long pre = block_exclusive_scan(mine, &tot);
+        if (has) {
+            unsigned s = base_s + (unsigned)(pre >> 32), it = base_i + (unsigned)pre;
+            const unsigned g = jb.wave_begin + L;
+            if (clear) {
+                w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, last, last_items * HR_CONSUMERS, j, 0u};
+                last = s;
+                last_items = ci;
+                s++;
+                it += ci;
+            }
+            w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, last, last_items * HR_CONSUMERS, j, 0u};
+            last = s;
+            last_items = ri;
+        }
+        base_s += (unsigned)(tot >> 32);
+        base_i += (unsigned)tot;
+    }
+    if (j < n_jobs && !failed && nw > 0) {
+        rg->last_key = w.wave_key[jb.wave_begin + nw - 1];
+        rg->used = 1;
     }
     if (threadIdx.x == 0) {
-        w.stages[tot_stages] = hr_stage{tot_items, n_waves, HR_STAGE_RECORDS, 0u};
-        if (n_waves > 0 && w.wave_key[0] < last_key) hr_set_error(&region->error, HR_ERR_ORDER);
-        w.ctl->n_stages = tot_stages;
-        w.ctl->total_items = failed ? 0u : tot_items;
-        if (!failed && n_waves > 0) {
-            region->last_key = w.wave_key[n_waves - 1];
-            region->used = 1;
-        }
+        w.stages[base_s] = hr_stage{base_i, 0u, HR_STAGE_RECORDS, 0u, HR_NO_DEP, 0u, 0u, 0u};
+        w.ctl->n_stages = base_s;
+        w.ctl->total_items = base_i;
     }
+}
+
+__global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev* regions)
+{
+    if (w.ctl->n_jobs == 1)
+        stages_one_job(w, regions);
+    else
+        stages_many_jobs(w, regions);
 }
 
 // ------------------------------------------------------------ the FSM checker
@@ -236,9 +361,10 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
 // warp prefetches its shadow lines into L2.
 
 struct TileInfo {
-    unsigned long long rb, re, key;  // record range and wave key of the tile
+    unsigned long long rb, re, key;  // record range (in the job's trace) and wave key of the tile
+    unsigned long long kb;           // the job's kernel base (shifted), to rebase record keys
     unsigned stage, type, item, valid;
-    unsigned skip, prev_need, pad0, pad1;
+    unsigned skip, dep, dep_need, region;
 };
 
 struct Acc {
@@ -394,20 +520,20 @@ __device__ __noinline__ unsigned retry_cas(unsigned long long* p, unsigned long 
     return attempts;
 }
 
-__device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record* trace, unsigned long long kb,
-                              uint4* s_rec, TileInfo* s_info, uint64_t* s_full, uint64_t* s_empty)
+__device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, TileInfo* s_info, uint64_t* s_full,
+                              uint64_t* s_empty)
 {
     const uint64_t pol = policy_evict_first();
     const unsigned total = w.ctl->total_items;
-    unsigned s = 0, s_begin = 0, s_end = 0, type = 0, prev_need = 0;
-    unsigned long long w_start = 0, w_end = 0, key = 0;
-    bool have = false;
+    unsigned s = 0, s_begin = 0, s_end = 0, type = 0, dep = HR_NO_DEP, dep_need = 0, region = 0;
+    unsigned long long w_start = 0, w_end = 0, key = 0, kb = 0;
+    const hr_record* trace = nullptr;
+    bool have = false, skip = false;
     unsigned pend = 0, pend_end = 0, polls = 0;
-    bool skip = *(volatile unsigned*)&region->error != 0;
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (it >= HR_RING &&
-            !mbar_wait(&s_empty[b], ((it / HR_RING) - 1) & 1u, &w.ctl->abort, &region->error)) {
+            !mbar_wait(&s_empty[b], ((it / HR_RING) - 1) & 1u, &w.ctl->abort, &regions[region].error)) {
             s_info[b].valid = 0;
             mbar_arrive(&s_full[b]);
             return;
@@ -415,7 +541,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
         if (pend == pend_end) {  // claim the next batch of tiles
             pend = atomicAdd(&w.ctl->ticket, HR_TICKET_BATCH);
             pend_end = min(pend + HR_TICKET_BATCH, total);
-            if (++polls % 8 == 0) skip = *(volatile unsigned*)&region->error != 0;
+            ++polls;
         }
         const unsigned t = pend++;
         if (t >= total || (polls % 8 == 0 && *(volatile unsigned*)&w.ctl->abort)) {
@@ -424,26 +550,36 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
             return;
         }
         if (!have || t >= s_end) {  // move to the stage holding ticket t
-            if (!have) s = 0;
             while (w.stages[s + 1].item_begin <= t) ++s;
             const hr_stage st = w.stages[s];
             s_begin = st.item_begin;
             s_end = w.stages[s + 1].item_begin;
             type = st.type;
-            prev_need = s ? (s_begin - w.stages[s - 1].item_begin) * HR_CONSUMERS : 0u;
+            dep = st.dep;
+            dep_need = st.dep_need;
+            const hr_jobd jb = w.jobs[st.job];
+            region = jb.region;
+            trace = jb.trace;
+            kb = jb.kb;
             w_start = w.wave_start[st.wave];
-            w_end = w.wave_start[st.wave + 1];
+            w_end = w.wave_end[st.wave];
             key = w.wave_key[st.wave];  // already rebased by the pre-pass
+            skip = *(volatile unsigned*)&regions[region].error != 0;
             have = true;
+        } else if (polls % 8 == 0) {
+            skip = *(volatile unsigned*)&regions[region].error != 0;
         }
         TileInfo info;
         info.valid = 1;
         info.stage = s;
         info.type = type;
         info.item = t - s_begin;
-        info.prev_need = prev_need;
+        info.dep = dep;
+        info.dep_need = dep_need;
+        info.region = region;
         info.skip = skip;
         info.key = key;
+        info.kb = kb;
         info.rb = w_start + (unsigned long long)info.item * HR_TILE;
         info.re = min(info.rb + HR_TILE, w_end);
         s_info[b] = info;
@@ -458,10 +594,9 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* region, const hr_record
 }
 
 template <bool AGG>
-__global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_region_dev* __restrict__ region, hr_work w,
-                                                                 const hr_record* __restrict__ trace,
-                                                                 const unsigned char* __restrict__ gtable,
-                                                                 unsigned long long kb)
+__global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_region_dev* __restrict__ regions,
+                                                                 hr_work w,
+                                                                 const unsigned char* __restrict__ gtable)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint4* s_rec = reinterpret_cast<uint4*>(smem);
@@ -484,17 +619,34 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
     __syncthreads();
 
     if (wid == HR_CONSUMERS) {
-        if (lane == 0) producer_loop(w, region, trace, kb, s_rec, s_info, s_full, s_empty);
+        if (lane == 0) producer_loop(w, regions, s_rec, s_info, s_full, s_empty);
         return;
     }
 
     // ---- consumer warp
-    const hr_geom g = region->geom;
-    unsigned long long* __restrict__ shadow = region->shadow;
-    const unsigned long long n_words = region->n_words;
+    unsigned cur = ~0u;  // region of the previous tile
+    hr_region_dev* region = nullptr;
+    hr_geom g{};
+    unsigned long long* shadow = nullptr;
+    unsigned long long n_words = 0;
     Acc* my_acc = s_acc + (size_t)wid * HR_RPL * 32;
-    int known = -1;  // highest stage index this warp has seen complete
+    unsigned known = HR_NO_DEP;  // last dependency this warp has seen complete
     unsigned long long c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
+    auto flush = [&]() {
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o2);
+            c_cas += __shfl_xor_sync(0xffffffffu, c_cas, o2);
+            c_retry += __shfl_xor_sync(0xffffffffu, c_retry, o2);
+            c_merged += __shfl_xor_sync(0xffffffffu, c_merged, o2);
+        }
+        if (lane == 0 && region) {
+            if (c_acc) atomicAdd(&region->counters[0], c_acc);
+            if (c_cas) atomicAdd(&region->counters[1], c_cas);
+            if (c_retry) atomicAdd(&region->counters[2], c_retry);
+            if (c_merged) atomicAdd(&region->counters[3], c_merged);
+        }
+        c_acc = c_cas = c_retry = c_merged = 0;
+    };
 
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
@@ -512,25 +664,34 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[b]);  // the slot may be refilled now
+        if (info.region != cur) {
+            flush();
+            cur = info.region;
+            region = regions + cur;
+            g = region->geom;
+            shadow = region->shadow;
+            n_words = region->n_words;
+        }
 
         const unsigned s = info.stage;
-        bool ready = s == 0 || (int)s - 1 <= known;
+        const unsigned dep = info.dep;
+        bool ready = dep == HR_NO_DEP || dep == known;
         if (!ready) {
             unsigned r = 0;
-            if (lane == 0) r = ld_acquire_u32(&w.stages[s - 1].done) >= info.prev_need;
+            if (lane == 0) r = ld_acquire_u32(&w.stages[dep].done) >= info.dep_need;
             ready = __shfl_sync(0xffffffffu, r, 0) != 0;
             __syncwarp();
-            if (ready) known = (int)s - 1;
+            if (ready) known = dep;
         }
 
         if (info.type == HR_STAGE_CLEAR && !info.skip) {
             if (!ready) {
                 bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
+                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 __syncwarp();
                 if (!ok) break;
-                known = (int)s - 1;
+                known = dep;
             }
             const unsigned long long span = HR_CLEAR_WORDS / HR_CONSUMERS;
             const unsigned long long wb = (unsigned long long)info.item * HR_CLEAR_WORDS + wid * span;
@@ -557,7 +718,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
                 const unsigned flags = v.w >> 24;
                 const bool in = info.rb + base + k * 32 < info.re;
                 const unsigned long long key = (((unsigned long long)(v.w & 0xFFFFu) << 32) |
-                                                ((unsigned long long)(v.z >> 16) << 16) | (v.z & 0xFFFFu)) + kb;
+                                                ((unsigned long long)(v.z >> 16) << 16) | (v.z & 0xFFFFu)) + info.kb;
                 bool a = in && op <= HR_A;
                 if (in) {
                     if (key != wkey) err = HR_ERR_ORDER;
@@ -618,11 +779,11 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
                 for (int k = 0; k < HR_RPL; ++k)
                     if (act[k]) asm volatile("prefetch.global.L2 [%0];" ::"l"(shadow + word[k]));
                 bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[s - 1].done, info.prev_need, &w.ctl->abort, &region->error);
+                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 __syncwarp();
                 if (!ok) break;
-                known = (int)s - 1;
+                known = dep;
             }
             unsigned long long o[HR_RPL], nv[HR_RPL];
             unsigned raced[HR_RPL], who[HR_RPL];
@@ -672,18 +833,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
         __syncwarp();
         if (lane == 0) red_release_add(&w.stages[s].done, 1u);
     }
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o2);
-        c_cas += __shfl_xor_sync(0xffffffffu, c_cas, o2);
-        c_retry += __shfl_xor_sync(0xffffffffu, c_retry, o2);
-        c_merged += __shfl_xor_sync(0xffffffffu, c_merged, o2);
-    }
-    if (lane == 0) {
-        if (c_acc) atomicAdd(&region->counters[0], c_acc);
-        if (c_cas) atomicAdd(&region->counters[1], c_cas);
-        if (c_retry) atomicAdd(&region->counters[2], c_retry);
-        if (c_merged) atomicAdd(&region->counters[3], c_merged);
-    }
+    flush();
 }
 
 __global__ void hr_sync_kernel(hr_region_dev* region)
@@ -727,24 +877,49 @@ int hr_check_grid_size(bool aggregate)
     return cached;
 }
 
-cudaError_t hr_launch_check(hr_region_dev* d_region, const hr_work& w, const hr_record* trace,
-                            unsigned long long n, unsigned kernel_base, const unsigned char* d_table,
-                            bool aggregate, int grid, cudaStream_t stream, cudaEvent_t before_check)
+void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int)
 {
-    const unsigned long long kb = (unsigned long long)kernel_base << 32;
-    unsigned G = 1024;
-    while ((n + G - 1) / G > HR_MAX_INTERVALS) G <<= 1;
-    const unsigned n_int = (unsigned)((n + G - 1) / G);
-    const unsigned scan_blocks = (n_int + 7) / 8 < 4096 ? (n_int + 7) / 8 : 4096;
-    hr_scan_intervals<<<scan_blocks, 256, 0, stream>>>(trace, n, G, n_int, w.counts, d_region, kb);
-    hr_scan_counts<<<1, 1024, 0, stream>>>(w.counts, n_int, w, d_region);
-    hr_write_waves<<<scan_blocks, 256, 0, stream>>>(trace, n, G, n_int, w, kb);
-    hr_build_stages<<<1, 1024, 0, stream>>>(w, d_region);
+    unsigned g = 1024;
+    if (budget < 1) budget = 1;
+    while ((n + g - 1) / g > budget && g < (1u << 30)) g <<= 1;
+    *G = g;
+    *n_int = (unsigned)((n + g - 1) / g);
+}
+
+template <unsigned CAP>
+static void launch_prepass(const JobParams<CAP>& P, unsigned total_int, hr_region_dev* d_regions, const hr_work& w,
+                           cudaStream_t stream)
+{
+    const unsigned blocks = (total_int + 7) / 8 < 4096 ? (total_int + 7) / 8 : 4096;
+    hr_scan_intervals<CAP><<<blocks, 256, 0, stream>>>(P, total_int, w, d_regions);
+    hr_scan_counts<<<1, 1024, 0, stream>>>(w, total_int, d_regions);
+    hr_write_waves<CAP><<<blocks, 256, 0, stream>>>(P, total_int, w);
+    hr_build_stages<<<1, 1024, 0, stream>>>(w, d_regions);
+}
+
+cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_jobd* jobs, unsigned n_jobs,
+                           const unsigned char* d_table, bool aggregate, int grid, cudaStream_t stream,
+                           cudaEvent_t before_check)
+{
+    if (n_jobs == 0 || n_jobs > HR_MAX_BATCH || n_jobs > w.max_jobs) return cudaErrorInvalidValue;
+    const unsigned total_int = jobs[n_jobs - 1].int_begin + jobs[n_jobs - 1].n_int;
+    if (total_int > w.max_intervals) return cudaErrorInvalidValue;
+    if (n_jobs == 1) {
+        JobParams<1> P;
+        P.n = 1;
+        P.job[0] = jobs[0];
+        launch_prepass(P, total_int, d_regions, w, stream);
+    } else {
+        static thread_local JobParams<HR_MAX_BATCH> P;  // 24 KB: off the stack; copied into the launch
+        P.n = n_jobs;
+        for (unsigned j = 0; j < n_jobs; ++j) P.job[j] = jobs[j];
+        launch_prepass(P, total_int, d_regions, w, stream);
+    }
     if (before_check) cudaEventRecord(before_check, stream);
     if (aggregate)
-        hr_check_kernel<true><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_region, w, trace, d_table, kb);
+        hr_check_kernel<true><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
     else
-        hr_check_kernel<false><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_region, w, trace, d_table, kb);
+        hr_check_kernel<false><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
     return cudaGetLastError();
 }
 

@@ -26,15 +26,16 @@ namespace {
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// layout of the scratch array
+// layout of the scratch array: region state, FSM table, then the pre-pass
+// scratch of one job (job slot, interval counts, wave table, stages, control)
 constexpr size_t OFF_REGION = 0;
 constexpr size_t OFF_TABLE = OFF_REGION + align256(sizeof(hr_region_dev));
-constexpr size_t OFF_CTL = OFF_TABLE + align256(2048);
-constexpr size_t OFF_COUNTS = OFF_CTL + align256(sizeof(hr_ctl));
-constexpr size_t OFF_START = OFF_COUNTS + align256(HR_MAX_INTERVALS * sizeof(unsigned));
-constexpr size_t OFF_KEY = OFF_START + align256((HR_NOALLOC_MAX_WAVES + 1) * sizeof(unsigned long long));
-constexpr size_t OFF_STAGES = OFF_KEY + align256(HR_NOALLOC_MAX_WAVES * sizeof(unsigned long long));
-constexpr size_t SCRATCH_BYTES = OFF_STAGES + align256((2 * HR_NOALLOC_MAX_WAVES + 1) * sizeof(hr_stage));
+constexpr size_t OFF_WORK = OFF_TABLE + align256(2048);
+constexpr size_t WORK_BYTES = align256(sizeof(hr_ctl)) + align256(sizeof(hr_jobd)) +
+                              align256(HR_MAX_INTERVALS * sizeof(unsigned)) +
+                              3 * align256(HR_NOALLOC_MAX_WAVES * sizeof(unsigned long long)) +
+                              align256((2 * HR_NOALLOC_MAX_WAVES + 1) * sizeof(hr_stage));
+constexpr size_t SCRATCH_BYTES = OFF_WORK + WORK_BYTES;
 static_assert(SCRATCH_BYTES == HR_NOALLOC_SCRATCH_BYTES, "header size must match the layout");
 
 static __device__ __align__(256) unsigned char hr_noalloc_scratch[SCRATCH_BYTES];
@@ -104,19 +105,18 @@ extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n
     if (setup_device(dev, &base) != cudaSuccess) return HR_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
     hr_region_dev* region = (hr_region_dev*)(base + OFF_REGION);
-    hr_work w{};
-    w.counts = (unsigned*)(base + OFF_COUNTS);
-    w.wave_start = (unsigned long long*)(base + OFF_START);
-    w.wave_key = (unsigned long long*)(base + OFF_KEY);
-    w.stages = (hr_stage*)(base + OFF_STAGES);
-    w.ctl = (hr_ctl*)(base + OFF_CTL);
-    w.max_waves = HR_NOALLOC_MAX_WAVES;
-    w.max_intervals = HR_MAX_INTERVALS;
+    const hr_work w = hr_work_at(base + OFF_WORK, 1, HR_MAX_INTERVALS, HR_NOALLOC_MAX_WAVES);
     const hr_geom g = hr_make_geom(block_dim, warp_size);
     hr_noalloc_begin<<<1, 1, 0, s>>>(region, (unsigned long long*)d_shadow, n_words, d_races, race_cap, g);
     cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess && n > 0)
-        e = hr_launch_check(region, w, d_trace, n, 0, base + OFF_TABLE, true, hr_check_grid_size(true), s, nullptr);
+    if (e == cudaSuccess && n > 0) {
+        hr_jobd job{};
+        job.trace = d_trace;
+        job.n = n;
+        job.region = 0;  // the region array is the single struct above
+        hr_plan_intervals(n, HR_MAX_INTERVALS, &job.G, &job.n_int);
+        e = hr_launch_jobs(region, w, &job, 1, base + OFF_TABLE, true, hr_check_grid_size(true), s, nullptr);
+    }
     if (e == cudaSuccess) {
         hr_noalloc_end<<<1, 1, 0, s>>>(region, d_result);
         e = cudaGetLastError();

@@ -38,6 +38,11 @@ class HrGeom(ctypes.Structure):
                 ("ws_magic", ctypes.c_uint64), ("bd_shift", ctypes.c_uint32), ("ws_shift", ctypes.c_uint32)]
 
 
+class HrJob(ctypes.Structure):
+    _fields_ = [("region", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("trace", ctypes.c_void_p),
+                ("n", ctypes.c_uint64)]
+
+
 class HrView(ctypes.Structure):
     """Mirror of hr_view (include/hirace_device.cuh): what an instrumented kernel gets by value."""
     _fields_ = [("shadow", ctypes.c_void_p), ("ring", ctypes.c_void_p), ("n_races", ctypes.c_void_p),
@@ -81,6 +86,10 @@ def load_library():
     lib.hr_profile_enable.argtypes = [P, i32]
     lib.hr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.hr_check_batch.argtypes = [P, ctypes.POINTER(HrJob), u32, P]
+    lib.hr_check_batch.restype = i32
+    lib.hr_batch_reserve.argtypes = [P, u32, u64]
+    lib.hr_batch_reserve.restype = i32
     lib.hr_device_view.argtypes = [P, u32, ctypes.POINTER(HrView)]
     lib.hr_device_view.restype = i32
     lib.hr_status_str.argtypes = [i32]
@@ -172,6 +181,23 @@ class Checker:
             fn = self._lib.hr_check_trace if aggregate else self._lib.hr_check_trace_plain
             rc = fn(self._ctx, region, ptr, n, st)
         self._check(rc, "hr_check_trace")
+
+    def check_batch(self, jobs, stream=None):
+        """Queue one batched check: ``jobs`` is a list of (region, device trace tensor)
+        with distinct regions."""
+        arr = (HrJob * max(1, len(jobs)))()
+        keep = []
+        for i, (region, trace) in enumerate(jobs):
+            ptr, n = _ptr_and_count(trace)
+            arr[i].region = region
+            arr[i].reserved = 0
+            arr[i].trace = ptr
+            arr[i].n = n
+            keep.append(trace)
+        self._check(self._lib.hr_check_batch(self._ctx, arr, len(jobs), _stream_handle(stream)), "hr_check_batch")
+
+    def batch_reserve(self, max_jobs: int, max_waves: int = 1 << 18):
+        self._check(self._lib.hr_batch_reserve(self._ctx, max_jobs, max_waves), "hr_batch_reserve")
 
     def sync(self, region: int, stream=None):
         self._check(self._lib.hr_sync(self._ctx, region, SYNC_KERNEL, _stream_handle(stream)), "hr_sync")
