@@ -202,6 +202,65 @@ def other_workloads(dev, reps=5):
     return out
 
 
+def batch_workload(dev, reps=3):
+    """512 traces (lengths log-uniform 10K..10M records, 60% shared-memory, 40%
+    global-memory) checked three ways: one launch per trace, one batched launch,
+    and the batched launch replayed from a CUDA graph.  Resets run outside the
+    timed spans."""
+    import torch
+    from paper_2401_04701_gb300 import hirace, tracegen as tg
+    jobs = tg.gen_batch(tg.seed_for(4))
+    n_acc = sum(int(np.count_nonzero(tr["op"] <= 2)) for tr, _ in jobs)
+    n_rec = sum(len(tr) for tr, _ in jobs)
+    regions = [dict(n_words=info["n_words"], block_dim=info["block_dim"], report_capacity=1 << 14)
+               for _, info in jobs]
+    d = [torch.from_numpy(tr.view(np.uint8)).to(dev) for tr, _ in jobs]
+    del jobs
+    out = {"traces": len(d), "records": n_rec, "accesses": n_acc}
+    stream = torch.cuda.current_stream(dev)
+    with hirace.Checker(regions, report_capacity=1 << 14) as ck:
+        ck.batch_reserve(len(d), 1 << 18)
+
+        def reset_all():
+            for i in range(len(d)):
+                ck.reset(i)
+            torch.cuda.synchronize()
+
+        def timed(fn):
+            tot = 0.0
+            for r in range(reps + 1):
+                reset_all()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                if r:
+                    tot += a.elapsed_time(b)
+            return tot / reps
+
+        per_trace_ms = timed(lambda: [ck.check_trace(i, t) for i, t in enumerate(d)])
+        races_single = sum(ck.report(i)[2] for i in range(len(d)))
+        batch_ms = timed(lambda: ck.check_batch(list(enumerate(d))))
+        races_batch = sum(ck.report(i)[2] for i in range(len(d)))
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(dev)
+        reset_all()
+        with torch.cuda.stream(s):
+            ck.check_batch(list(enumerate(d)), stream=s)
+        torch.cuda.synchronize()
+        reset_all()
+        with torch.cuda.graph(g, stream=s):
+            ck.check_batch(list(enumerate(d)), stream=s)
+        graph_ms = timed(lambda: g.replay())
+        races_graph = sum(ck.report(i)[2] for i in range(len(d)))
+    for name, ms in (("one_launch_per_trace", per_trace_ms), ("batched_launch", batch_ms),
+                     ("batched_graph_replay", graph_ms)):
+        out[name] = {"ms": ms, "accesses_per_s": n_acc / (ms / 1e3)}
+    out["races"] = {"per_trace": races_single, "batched": races_batch, "graph": races_graph}
+    return out
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -338,6 +397,7 @@ def run_gpu(args, rank, world, local_rank):
         line["instrumented_slowdown"] = instrumented_slowdown(dev)
     if args.all_workloads:
         line["other_workloads"] = other_workloads(dev)
+        line["batch_workload"] = batch_workload(dev)
     print(json.dumps(line), flush=True)
     ck.close()
 

@@ -266,8 +266,9 @@ def gen_global_mix(seed: int, inject: bool = True, n_blocks: int = 1024, block_d
 
     injected = np.zeros(0, np.int64)
     if inject:
-        n_inj = int(inject_frac * n_words)
         random_idx = np.flatnonzero((cls == 0) | (cls == 1))
+        # short traces have fewer random accesses than the word-based count asks for
+        n_inj = min(int(inject_frac * n_words), len(random_idx) // 2)
         source_pool = np.flatnonzero((cls == 0) | (cls >= 2))
         carriers = rng.choice(random_idx, size=n_inj, replace=False)
         carrier_mask = np.zeros(len(rec), bool)
@@ -438,3 +439,50 @@ def gen_powerlaw_push(seed: int, log2_vertices: int = 22, avg_degree: int = 16, 
         trace["op"][injected] = OP_W
     info = dict(n_words=n, block_dim=block_dim, n_threads=n, injected=injected, edges=m)
     return trace, info
+
+
+# --------------------------------------------------------------------------
+# Workload 4: a batch of independent traces of uneven length
+# --------------------------------------------------------------------------
+
+def gen_batch(seed: int, n_traces: int = 512, min_len: int = 10_000, max_len: int = 10_000_000,
+              shared_frac: float = 0.6, max_rate: float = 0.01):
+    """``n_traces`` independent traces with lengths log-uniform in [min_len, max_len].
+
+    A ``shared_frac`` share are shared-memory tree reductions (block size 64..1024
+    in steps of 32, a 4..48 KB array of 4-byte words, repetitions set to reach
+    the drawn length); the rest are global-memory traces shaped like
+    ``gen_global_mix`` over a 1..64 MB region (log-uniform), with the per-thread
+    access count scaled toward the drawn length.  Each trace draws its race
+    injection rate uniformly in [0, max_rate].
+
+    Returns a list of (trace, info) with info = dict(n_words, block_dim, kind, target).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n_traces):
+        target = int(np.exp(rng.uniform(np.log(min_len), np.log(max_len))))
+        rate = float(rng.uniform(0.0, max_rate))
+        sub = int(rng.integers(0, 2**31))
+        if rng.random() < shared_frac:
+            block = int(rng.integers(2, 33)) * 32
+            kb = int(rng.integers(4, 49))
+            segments = max(1, (kb * 256) // block)
+            n_epochs = int(np.log2(block))
+            per_rep = segments * 3 * sum((block // 2) >> k for k in range(n_epochs))
+            reps = max(1, target // max(1, per_rep))
+            trace, info = gen_tree_reduction(sub, inject=rate > 0, segments=segments, block_dim=block, reps=reps,
+                                             p_unit=rate, force=False)
+            info = dict(n_words=info["n_words"], block_dim=block, kind="shared", target=target)
+        else:
+            mb = float(np.exp(rng.uniform(0.0, np.log(64.0))))
+            n_blocks = max(1, int(mb * 262144) // 65536)
+            threads = n_blocks * 256
+            per_thread = max(1, target // threads)
+            epochs = int(np.clip(per_thread // 32, 1, 8))
+            slots = int(np.clip(per_thread // (4 * epochs), 1, 8))
+            trace, info = gen_global_mix(sub, inject=rate > 0, n_blocks=n_blocks, epochs=epochs, slots=slots,
+                                         inject_frac=rate)
+            info = dict(n_words=info["n_words"], block_dim=256, kind="global", target=target)
+        out.append((trace, info))
+    return out

@@ -120,3 +120,16 @@ def test_batch_in_cuda_graph(oracle_mod, hr):
             for i in range(len(jobs)):
                 races, status, n_total, _ = ck.report(i)
                 assert status == hr.HR_OK and hr.race_keys(races) == want[i]
+
+
+def test_uneven_batch_workload(oracle_mod, hr):
+    """64 traces of the batch workload (lengths 1K..200K, shared and global kinds)."""
+    jobs = tg.gen_batch(tg.seed_for(4, 1), n_traces=64, min_len=1000, max_len=200_000)
+    regions = [dict(n_words=info["n_words"], block_dim=info["block_dim"]) for _, info in jobs]
+    dev = [to_dev(tr) for tr, _ in jobs]
+    with hr.Checker(regions, report_capacity=1 << 16) as ck:
+        ck.check_batch(list(enumerate(dev)))
+        for i, (tr, info) in enumerate(jobs):
+            want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, info["block_dim"]))
+            races, status, n_total, _ = ck.report(i)
+            assert status == hr.HR_OK and hr.race_keys(races) == want, i
