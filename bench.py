@@ -261,6 +261,35 @@ def batch_workload(dev, reps=3):
     return out
 
 
+def serving_workload(dev, duration, rate=2000.0):
+    """Poisson arrivals (rate/s for `duration` s): 75% trace checks (prefixes of
+    10K..50M records of pooled tree-reduction, global-mix and power-law traces),
+    25% instrumented kernels (grid 64..4096 x 256); 64 region slots, 64 GB
+    shadow budget, 4M-record chunks.  Then the same arrivals served one request
+    at a time (whole trace per check) for at most twice as long."""
+    from paper_2401_04701_gb300 import serving
+    pool = serving.TracePool(dev, scale="full")
+    reqs = serving.make_requests(tg_seed(5), rate=rate, duration=duration)
+    srv = serving.Server(pool, dev, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30, chunk_records=1 << 22)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    out = {"requests": len(reqs), "rate_per_s": rate, "duration_s": duration,
+           "continuous_batching": dict(serving.summarize(res, wall), iterations=srv.iterations, wall_s=wall)}
+    ser = serving.Server(pool, dev, n_slots=2, slot_words=1 << 26, budget_bytes=64 << 30)
+    t0 = time.perf_counter()
+    sres = ser.run_serial(reqs, time_limit=2 * duration)
+    swall = time.perf_counter() - t0
+    out["serial_one_at_a_time"] = dict(serving.summarize(sres, swall), wall_s=swall,
+                                       not_served=len(reqs) - len(sres))
+    return out
+
+
+def tg_seed(k):
+    from paper_2401_04701_gb300 import tracegen as tg
+    return tg.seed_for(k)
+
+
 def run_reference(args, rank, world):
     """Reference arm: the CPU oracle as it stands, on the host cores."""
     if rank != 0:
@@ -398,6 +427,7 @@ def run_gpu(args, rank, world, local_rank):
     if args.all_workloads:
         line["other_workloads"] = other_workloads(dev)
         line["batch_workload"] = batch_workload(dev)
+        line["serving"] = serving_workload(dev, args.serving_seconds)
     print(json.dumps(line), flush=True)
     ck.close()
 
@@ -413,6 +443,8 @@ def main():
     ap.add_argument("--no-instrumented", action="store_true")
     ap.add_argument("--all-workloads", action="store_true",
                     help="also time the tree-reduction and power-law workloads (adds ~2 min)")
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
+                    help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--blocks", type=int, default=1024,
                     help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()

@@ -222,6 +222,16 @@ hr_status hr_counters(hr_ctx* ctx, uint32_t region, uint64_t out[4]);
  * and error cleared, kernel ordinal back to 0.  Asynchronous. */
 hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream);
 
+/*
+ * hr_region_reconfigure - give a region new geometry (n_words up to the
+ * n_words it was created with, block_dim, warp_size) and reset it like
+ * hr_reset, without allocating: lets a server reuse pre-allocated region
+ * slots for jobs of different shapes.  Stream-ordered.  HR_ERR_INVALID if
+ * n_words exceeds the region's allocation.
+ */
+hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_t n_words, uint32_t block_dim,
+                                uint32_t warp_size, hr_stream_t stream);
+
 /* hr_destroy - synchronise and free everything the context owns. */
 hr_status hr_destroy(hr_ctx* ctx);
 

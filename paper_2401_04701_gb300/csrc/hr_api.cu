@@ -16,6 +16,7 @@ struct RegionHost {
     unsigned long long* shadow = nullptr;
     hr_race* ring = nullptr;
     unsigned long long ring_cap = 0;
+    unsigned long long capacity = 0;      // shadow words allocated (n_words may be reconfigured below it)
     void* work_mem = nullptr;
     hr_work work{};
     unsigned kernel = 0;                  // kernel ordinal seen by device views
@@ -141,6 +142,7 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         r.desc = regions[i];
         r.ring_cap = regions[i].report_capacity ? regions[i].report_capacity : report_capacity;
         r.d = c->d_regions + i;
+        r.capacity = r.desc.n_words;
         e = cudaMalloc(&r.shadow, r.desc.n_words * sizeof(unsigned long long));
         if (e == cudaSuccess) e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
         // scratch of one trace check: job table, interval counts, wave table, stages, control block
@@ -359,6 +361,25 @@ extern "C" hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream)
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();  // report only errors of this call's launches
     cudaError_t e = hr_launch_reset(r.d, r.shadow, r.desc.n_words, s);
+    if (e == cudaSuccess) e = mark_done(r, s);
+    r.kernel = 0;
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_t n_words, uint32_t block_dim,
+                                           uint32_t warp_size, hr_stream_t stream)
+{
+    if (!valid_region(ctx, region)) return HR_ERR_INVALID;
+    RegionHost& r = ctx->regions[region];
+    if (n_words == 0 || n_words > r.capacity || block_dim == 0 || warp_size == 0 || warp_size > 32)
+        return HR_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();  // report only errors of this call's launches
+    r.desc.n_words = n_words;
+    r.desc.block_dim = block_dim;
+    r.desc.warp_size = warp_size;
+    cudaError_t e = hr_launch_reconfigure(r.d, n_words, hr_make_geom(block_dim, warp_size), s);
+    if (e == cudaSuccess) e = hr_launch_reset(r.d, r.shadow, n_words, s);
     if (e == cudaSuccess) e = mark_done(r, s);
     r.kernel = 0;
     return cuda_status(e);

@@ -169,3 +169,5 @@ constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
 cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long n_words,
                             cudaStream_t stream);
+cudaError_t hr_launch_reconfigure(hr_region_dev* d_region, unsigned long long n_words, hr_geom geom,
+                                  cudaStream_t stream);

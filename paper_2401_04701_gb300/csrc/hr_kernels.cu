@@ -854,6 +854,12 @@ __global__ void hr_reset_state(hr_region_dev* region)
     for (int i = 0; i < 4; ++i) region->counters[i] = 0;
 }
 
+__global__ void hr_reconfigure_state(hr_region_dev* region, unsigned long long n_words, hr_geom geom)
+{
+    region->n_words = n_words;
+    region->geom = geom;
+}
+
 int g_grid[2] = {0, 0};
 
 }  // namespace
@@ -920,6 +926,13 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_
         hr_check_kernel<true><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
     else
         hr_check_kernel<false><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
+    return cudaGetLastError();
+}
+
+cudaError_t hr_launch_reconfigure(hr_region_dev* d_region, unsigned long long n_words, hr_geom geom,
+                                  cudaStream_t stream)
+{
+    hr_reconfigure_state<<<1, 1, 0, stream>>>(d_region, n_words, geom);
     return cudaGetLastError();
 }
 

@@ -90,6 +90,8 @@ def load_library():
     lib.hr_check_batch.restype = i32
     lib.hr_batch_reserve.argtypes = [P, u32, u64]
     lib.hr_batch_reserve.restype = i32
+    lib.hr_region_reconfigure.argtypes = [P, u32, u64, u32, u32, P]
+    lib.hr_region_reconfigure.restype = i32
     lib.hr_device_view.argtypes = [P, u32, ctypes.POINTER(HrView)]
     lib.hr_device_view.restype = i32
     lib.hr_status_str.argtypes = [i32]
@@ -221,6 +223,12 @@ class Checker:
         buf = (ctypes.c_uint64 * 4)()
         self._check(self._lib.hr_counters(self._ctx, region, ctypes.byref(buf)), "hr_counters")
         return dict(accesses=buf[0], cas=buf[1], retries=buf[2], merged=buf[3])
+
+    def reconfigure(self, region: int, n_words: int, block_dim: int, warp_size: int = 32, stream=None):
+        """Reuse a region for a job of another shape (n_words within its allocation)."""
+        self._check(self._lib.hr_region_reconfigure(self._ctx, region, n_words, block_dim, warp_size,
+                                                    _stream_handle(stream)), "hr_region_reconfigure")
+        self.regions[region] = dict(self.regions[region], n_words=n_words, block_dim=block_dim, warp_size=warp_size)
 
     def reset(self, region: int, stream=None):
         self._check(self._lib.hr_reset(self._ctx, region, _stream_handle(stream)), "hr_reset")
