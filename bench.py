@@ -261,16 +261,24 @@ def batch_workload(dev, reps=3):
     return out
 
 
-def serving_workload(dev, duration, rate=2000.0):
+def serving_workload(dev, duration, rates=(2000.0, 8000.0)):
+    """The serving measurement at the workload's 2000 requests/s and at a higher
+    rate where one-at-a-time service saturates."""
+    from paper_2401_04701_gb300 import serving
+    pool = serving.TracePool(dev, scale="full")
+    return {"%d_per_s" % r: serving_run(dev, pool, duration, r) for r in rates}
+
+
+def serving_run(dev, pool, duration, rate):
     """Poisson arrivals (rate/s for `duration` s): 75% trace checks (prefixes of
     10K..50M records of pooled tree-reduction, global-mix and power-law traces),
     25% instrumented kernels (grid 64..4096 x 256); 64 region slots, 64 GB
-    shadow budget, 4M-record chunks.  Then the same arrivals served one request
-    at a time (whole trace per check) for at most twice as long."""
+    shadow budget, 64M records per iteration shared by the active jobs (at
+    least 1M each).  Then the same arrivals served one request at a time (whole
+    trace per check) for at most twice as long."""
     from paper_2401_04701_gb300 import serving
-    pool = serving.TracePool(dev, scale="full")
     reqs = serving.make_requests(tg_seed(5), rate=rate, duration=duration)
-    srv = serving.Server(pool, dev, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30, chunk_records=1 << 22)
+    srv = serving.Server(pool, dev, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30, chunk_records=1 << 20)
     t0 = time.perf_counter()
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
@@ -443,6 +451,7 @@ def main():
     ap.add_argument("--no-instrumented", action="store_true")
     ap.add_argument("--all-workloads", action="store_true",
                     help="also time the tree-reduction and power-law workloads (adds ~2 min)")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--blocks", type=int, default=1024,
@@ -455,6 +464,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"serving": serving_workload(torch.device("cuda", local_rank), args.serving_seconds)}))
         return
     if world > 1:
         import torch.distributed as dist

@@ -67,6 +67,7 @@ struct hr_ctx {
     hr_region_dev* d_regions = nullptr;
     unsigned char* d_table = nullptr;
     bool profile = false;
+    cudaStream_t copies = nullptr;     // non-blocking stream for report copies (never waits on user streams)
     void* batch_mem = nullptr;         // scratch of hr_check_batch (allocated on first use)
     hr_work batch{};
     unsigned batch_jobs = 0;
@@ -104,6 +105,7 @@ static void free_ctx(hr_ctx* c)
             cudaEventDestroy(p.mid);
             cudaEventDestroy(p.end);
         }
+    if (c->copies) cudaStreamDestroy(c->copies);
     cudaFree(c->batch_mem);
     cudaFree(c->d_regions);
     cudaFree(c->d_table);
@@ -132,7 +134,8 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
     hr_status st = HR_OK;
     uint8_t table[2048];
     hr_fsm_table(table, nullptr);
-    cudaError_t e = cudaMalloc(&c->d_table, sizeof table);
+    cudaError_t e = cudaStreamCreateWithFlags(&c->copies, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_table, sizeof table);
     if (e == cudaSuccess) e = cudaMemcpy(c->d_table, table, sizeof table, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_regions, sizeof(hr_region_dev) * n_regions);
     const unsigned max_waves = max_waves_setting();
@@ -321,7 +324,8 @@ static hr_status fetch_region(hr_ctx* ctx, uint32_t region, hr_region_dev* out)
 {
     RegionHost& r = ctx->regions[region];
     cudaError_t e = r.captured ? cudaDeviceSynchronize() : cudaEventSynchronize(r.done);
-    if (e == cudaSuccess) e = cudaMemcpy(out, r.d, sizeof *out, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, r.d, sizeof *out, cudaMemcpyDeviceToHost, ctx->copies);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copies);
     return cuda_status(e);
 }
 
@@ -336,7 +340,8 @@ extern "C" hr_status hr_report(hr_ctx* ctx, uint32_t region, hr_race* host_out, 
     unsigned long long avail = h.n_races < r.ring_cap ? h.n_races : r.ring_cap;
     unsigned long long ncopy = avail < cap ? avail : cap;
     if (ncopy) {
-        cudaError_t e = cudaMemcpy(host_out, r.ring, ncopy * sizeof(hr_race), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpyAsync(host_out, r.ring, ncopy * sizeof(hr_race), cudaMemcpyDeviceToHost, ctx->copies);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->copies);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (n_total) *n_total = h.n_races;

@@ -16,6 +16,9 @@ Each loop iteration gathers the next chunk of every active trace job into one
 batched check (``hr_check_batch``: one persistent launch, stages interleaved
 across jobs), so requests that arrive while others run join the next
 iteration; up to ``max_inflight`` iterations are queued on the GPU at once.
+An iteration shares a record budget among the active jobs (each gets at least
+one chunk), so a lone job is checked whole and iterations stay short under
+load.
 Latency is measured from the request's arrival to the moment the host sees
 its last chunk complete.
 """
@@ -48,7 +51,7 @@ class Result:
     rid: int
     kind: str
     status: int
-    races: set
+    races: np.ndarray          # the request's race records (hirace.RACE_DTYPE)
     n_races: int
     accesses: int
     arrival: float
@@ -58,6 +61,10 @@ class Result:
     @property
     def latency(self):
         return self.done - self.arrival
+
+    def keys(self) -> set:
+        """{(kernel, word, epoch)} of the request's races."""
+        return hirace.race_keys(self.races)
 
 
 class TracePool:
@@ -110,13 +117,14 @@ def kernel_accesses(name, threads):
 
 class Server:
     def __init__(self, pool: TracePool, device, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30,
-                 chunk_records=1 << 22, max_inflight=2):
+                 chunk_records=1 << 22, max_inflight=2, iteration_records=1 << 26):
         import torch
         self.pool = pool
         self.device = device
         self.n_slots = n_slots
         self.budget = budget_bytes
-        self.chunk = chunk_records
+        self.chunk = chunk_records          # smallest chunk a job gets per iteration
+        self.iteration_records = iteration_records  # records shared by the active jobs per iteration
         self.max_inflight = max_inflight
         self.ck = hirace.Checker([dict(n_words=slot_words, block_dim=256, report_capacity=RING)] * n_slots,
                                  report_capacity=RING)
@@ -193,9 +201,12 @@ class Server:
         if not self.active or len(self.inflight) >= self.max_inflight:
             return False
         batch, finishing = [], []
+        # share the iteration's record budget: a lone job takes its whole remainder,
+        # many jobs take at least one chunk each
+        share = max(self.chunk, self.iteration_records // len(self.active))
         for slot, job in list(self.active.items()):
             a = job["next"]
-            b = min(job["length"], a + self.chunk)
+            b = min(job["length"], a + share)
             batch.append((slot, job["dev"][a * 16: b * 16]))
             job["next"] = b
             if b >= job["length"]:
@@ -215,15 +226,34 @@ class Server:
             for slot, job in finished:
                 races, status, n_total, _ = self.ck.report(slot)
                 req = job["req"]
-                self.results[req.rid] = Result(req.rid, req.kind, status, hirace.race_keys(races), n_total,
+                self.results[req.rid] = Result(req.rid, req.kind, status, races.copy(), n_total,
                                                job["accesses"], req.arrival, job["admitted"], t)
                 self.free.append(slot)
                 self.used -= job["need"]
 
     # ------------------------------------------------------------- driving
-    def run(self, requests, time_limit=None):
+    def warmup(self):
+        """One untimed request of every trace kind and every kernel: first launches
+        load kernel modules and set up generators, which should not count as
+        request latency."""
+        reqs = [Request(-1 - i, 0.0, "trace", name, 200_000, i) for i, name in enumerate(self.pool.entries)]
+        reqs += [Request(-10 - i, 0.0, "kernel", name, 1 << 16, i) for i, name in enumerate(KERNELS)]
+        saved = self.results
+        self.results = {}
+        self._drive(reqs, None)
+        self._drive(reqs, None, serial=True)
+        self.results = saved
+
+    def run(self, requests, time_limit=None, warm=True):
         """Serve ``requests`` (sorted by arrival) in real time; returns results by rid."""
+        if warm:
+            self.warmup()
+        return self._drive(requests, time_limit)
+
+    def _drive(self, requests, time_limit, serial=False):
         import torch
+        if serial:
+            return self._serial(requests, time_limit)
         torch.cuda.synchronize(self.device)
         self.t0 = time.perf_counter()
         pending = collections.deque(requests)
@@ -242,8 +272,13 @@ class Server:
         self._poll()
         return self.results
 
-    def run_serial(self, requests, time_limit=None):
+    def run_serial(self, requests, time_limit=None, warm=True):
         """One request at a time, in arrival order, whole trace in one check."""
+        if warm:
+            self.warmup()
+        return self._serial(requests, time_limit)
+
+    def _serial(self, requests, time_limit):
         import torch
         torch.cuda.synchronize(self.device)
         self.t0 = time.perf_counter()
@@ -253,11 +288,12 @@ class Server:
                 break
             if req.arrival > now:
                 time.sleep(req.arrival - now)
-            old_chunk, self.chunk = self.chunk, 1 << 40
+            old = self.chunk, self.iteration_records
+            self.chunk = self.iteration_records = 1 << 40
             self.submit(req)
             self._admit()
             self._launch_iteration()
-            self.chunk = old_chunk
+            self.chunk, self.iteration_records = old
             while self.inflight:
                 self.inflight[0][0].synchronize()
                 self._poll()

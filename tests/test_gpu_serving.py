@@ -39,12 +39,12 @@ def test_alone_equals_mix(oracle_mod, env):
     for r in reqs:
         solo = serving.Request(r.rid, 0.0, r.kind, r.source, r.length, r.seed)
         alone_server.results = {}
-        got = alone_server.run([solo])[r.rid]
+        got = alone_server.run([solo], warm=False)[r.rid]
         m = mix[r.rid]
         assert got.status == m.status == 0, r
-        assert got.races == m.races and got.n_races == m.n_races, r
+        assert got.keys() == m.keys() and got.n_races == m.n_races, r
         if r.kind == "trace" and r.length <= 400_000:
             e = pool.entries[r.source]
             prefix = e["host"][: min(r.length, e["n"])]
             want = oracle_mod.race_keys(oracle_mod.bruteforce(prefix, e["block_dim"]))
-            assert m.races == want, r
+            assert m.keys() == want, r
