@@ -40,6 +40,32 @@ ALG_BYTES_PER_ACCESS = 32   # 16 B record + 8 B shadow read + 8 B shadow write
 ALG_BYTES_PER_SYNC = 16     # a barrier record is streamed, not an access
 
 
+KERNEL_SOURCES = ("paper_2401_04701_gb300/csrc/hr_kernels.cu", "paper_2401_04701_gb300/csrc/hr_internal.h",
+                  "include/hirace_device.cuh")
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic():
+    """DRAM bytes per checker launch from the committed ncu capture, or None when
+    the kernel sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("kernel_sources_sha256") == kernel_sources_sha():
+            return int(t["dram_bytes_read"]) + int(t["dram_bytes_write"])
+    except Exception:
+        pass
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -419,7 +445,8 @@ def run_gpu(args, rank, world, local_rank):
                    "l2": "inputs larger than L2 (1.2 GB trace, 512 MB shadow), no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
-                     "frac": achieved / p_hbm, "traffic": None, "kernel": "hr_check_kernel<true>",
+                     "frac": achieved / p_hbm, "traffic": measured_traffic() if args.blocks == 1024 else None,
+                     "kernel": "hr_check_kernel<true>",
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
@@ -452,6 +479,8 @@ def main():
     ap.add_argument("--all-workloads", action="store_true",
                     help="also time the tree-reduction and power-law workloads (adds ~2 min)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
+    ap.add_argument("--probe-memory", action="store_true",
+                    help="random 8-byte load/CAS/store rates over 16..512 MB arrays, then exit")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--blocks", type=int, default=1024,
@@ -464,6 +493,12 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.probe_memory:
+        import torch
+        from paper_2401_04701_gb300 import hirace
+        torch.cuda.set_device(local_rank)
+        print(json.dumps({"random_access_G_ops_per_s": hirace.probe_random_access(torch.device("cuda", local_rank))}))
         return
     if args.serving_only:
         import torch

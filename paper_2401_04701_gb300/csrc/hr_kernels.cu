@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
 // their records sit in registers, and apply them to the shadow.  A tile of
 // wave w may only touch the shadow once every tile of the previous stage is
 // done (per-warp completion counts with release/acquire); while it waits, the
-// warp prefetches its shadow lines into L2.
+// warp touches its shadow words so they sit in L2.
 
 struct TileInfo {
     unsigned long long rb, re, key;  // record range (in the job's trace) and wave key of the tile
@@ -773,11 +773,14 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
             __syncwarp();
 
             if (!ready) {
-                // the previous stage is still running: pull this tile's shadow lines
-                // into L2 while waiting for it, then load them fresh
+                // the previous stage is still running: touch this tile's shadow words
+                // (one 32-byte sector each, value discarded) so they sit in L2 while
+                // waiting for it, then load them fresh
 #pragma unroll
                 for (int k = 0; k < HR_RPL; ++k)
-                    if (act[k]) asm volatile("prefetch.global.L2 [%0];" ::"l"(shadow + word[k]));
+                    if (act[k])
+                        asm volatile("{\n\t.reg .b64 t;\n\tld.relaxed.gpu.global.u64 t, [%0];\n\t}" ::"l"(shadow + word[k])
+                                     : "memory");
                 bool ok = true;
                 if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;

@@ -136,3 +136,77 @@ extern "C" int hrw_reduce(const hr_view* view, float* data, uint32_t n, uint32_t
         reduce_kernel<false><<<grid, block, 0, s>>>(null_view(), data, n, drop_level);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
+
+// ---------------------------------------------------------------------------
+// Memory-system probe: random 8-byte accesses over an array of 2^lg words.
+// mode 0 relaxed load, 1 CAS, 2 load then CAS, 3 atomicAdd (no return),
+// 4 plain store.  Indices are hash(i) & (2^lg - 1), always in bounds.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ uint32_t probe_hash(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+template <int MODE>
+__global__ void probe_kernel(unsigned long long* a, uint32_t mask, uint32_t total, unsigned long long* sink)
+{
+    constexpr int PER = 8;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    unsigned long long acc = 0;
+    for (uint32_t base = i; base < total; base += stride * PER) {
+        uint32_t idx[PER];
+        unsigned long long v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) idx[k] = probe_hash(base + k * stride) & mask;
+        if (MODE == 0 || MODE == 2) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) v[k] = hr_ld_relaxed(a + idx[k]);
+        }
+        if (MODE == 1) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) v[k] = atomicCAS(a + idx[k], 0ull, (unsigned long long)(base + k));
+        } else if (MODE == 2) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) v[k] = atomicCAS(a + idx[k], v[k], v[k] + 1);
+        } else if (MODE == 3) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) atomicAdd(a + idx[k], 1ull);
+        } else if (MODE == 4) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) a[idx[k]] = base + k;
+        }
+        if (MODE <= 2) {
+#pragma unroll
+            for (int k = 0; k < PER; ++k) acc += v[k];
+        }
+    }
+    if (acc == 0x123456789ull) *sink = acc;
+}
+
+}  // namespace
+
+// Launch one probe pass: `total` random accesses over a[0 .. 2^lg).  a must
+// hold at least 2^lg words and sink one word.  Returns 0, 1 for bad arguments.
+extern "C" int hrw_probe(int mode, unsigned long long* a, uint32_t lg, uint32_t total, unsigned long long* sink,
+                         uint32_t grid, uint32_t block, hr_stream_t stream)
+{
+    if (!a || !sink || lg > 31 || mode < 0 || mode > 4 || grid == 0 || block == 0 || block > 1024) return 1;
+    const uint32_t mask = (lg == 32) ? 0xFFFFFFFFu : ((1u << lg) - 1u);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (mode) {
+    case 0: probe_kernel<0><<<grid, block, 0, s>>>(a, mask, total, sink); break;
+    case 1: probe_kernel<1><<<grid, block, 0, s>>>(a, mask, total, sink); break;
+    case 2: probe_kernel<2><<<grid, block, 0, s>>>(a, mask, total, sink); break;
+    case 3: probe_kernel<3><<<grid, block, 0, s>>>(a, mask, total, sink); break;
+    default: probe_kernel<4><<<grid, block, 0, s>>>(a, mask, total, sink); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}

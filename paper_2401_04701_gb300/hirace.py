@@ -293,7 +293,8 @@ def load_workloads():
     lib.hrw_stencil.argtypes = [VP, P, P, u32, u32, u32, P]
     lib.hrw_histogram.argtypes = [VP, P, u32, P, u32, u32, P]
     lib.hrw_reduce.argtypes = [VP, P, u32, u32, i32, P]
-    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce):
+    lib.hrw_probe.argtypes = [i32, P, u32, u32, P, u32, u32, P]
+    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce, lib.hrw_probe):
         f.restype = i32
     _wl = lib
     return lib
@@ -318,3 +319,35 @@ def run_reduce(view, d_data, block=256, drop_level=-1, stream=None):
                                      d_data.numel(), block, drop_level, _stream_handle(stream))
     if rc:
         raise RuntimeError("hrw_reduce failed (%d)" % rc)
+
+
+PROBE_MODES = ("load", "cas64", "load+cas64", "atomicAdd64", "store64")
+
+
+def probe_random_access(device, log2_words=(21, 23, 24, 25, 26), total=1 << 26, reps=3):
+    """Random 8-byte access rates (G ops/s) over arrays of 2^lg words, per mode."""
+    import torch
+    lib = load_workloads()
+    n = 1 << max(log2_words)
+    a = torch.zeros(n, dtype=torch.int64, device=device)
+    sink = torch.zeros(1, dtype=torch.int64, device=device)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    stream = torch.cuda.current_stream(device)
+    out = {}
+    for lg in log2_words:
+        row = {}
+        for mode, name in enumerate(PROBE_MODES):
+            times = []
+            for r in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rc = lib.hrw_probe(mode, a.data_ptr(), lg, total, sink.data_ptr(), sms * 8, 256, stream.cuda_stream)
+                e1.record(stream)
+                torch.cuda.synchronize(device)
+                if rc:
+                    raise RuntimeError("hrw_probe failed (%d)" % rc)
+                if r:
+                    times.append(e0.elapsed_time(e1))
+            row[name] = total / (sum(times) / len(times) / 1e3) / 1e9
+        out["%d_MB" % ((8 << lg) >> 20)] = row
+    return out
