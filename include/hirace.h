@@ -236,6 +236,20 @@ hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_t n_words, 
 hr_status hr_destroy(hr_ctx* ctx);
 
 /*
+ * hr_set_limits - bounds of the device-side waits and retries of this
+ * context's later checks (Sec. III-A: checking stops with a report rather than
+ * running on).  wait_ns (> 0, default 4e9) bounds every wait of a CTA on the
+ * previous stage or on its copy pipeline; when it runs out the launch winds
+ * down and the region reports HR_ERR_TIMEOUT.  cas_retry_cap (default 4096)
+ * bounds the CAS retries of one update; beyond it the region reports
+ * HR_ERR_CONTENTION.  test_flags is a test hook: HR_TEST_HOLD_STAGE makes the
+ * second stage of a single-trace check wait for a completion that never comes,
+ * so the bounded wait runs out; leave it 0 otherwise.
+ */
+#define HR_TEST_HOLD_STAGE 1u
+hr_status hr_set_limits(hr_ctx* ctx, uint64_t wait_ns, uint32_t cas_retry_cap, uint32_t test_flags);
+
+/*
  * Profiling (no paper counterpart; measurement support).  With profiling on,
  * every check call records CUDA events on its stream around the wave
  * pre-pass and around the FSM kernel.  hr_profile_read waits for those

@@ -67,6 +67,9 @@ struct hr_ctx {
     hr_region_dev* d_regions = nullptr;
     unsigned char* d_table = nullptr;
     bool profile = false;
+    unsigned long long wait_ns = HR_DEFAULT_WAIT_NS;
+    unsigned cas_cap = HR_DEFAULT_CAS_CAP;
+    unsigned test_flags = 0;
     cudaStream_t copies = nullptr;     // non-blocking stream for report copies (never waits on user streams)
     void* batch_mem = nullptr;         // scratch of hr_check_batch (allocated on first use)
     hr_work batch{};
@@ -198,7 +201,11 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     ProfiledCall pc{};
     if (ctx->profile) pc = take_events(ctx);
     if (ctx->profile) cudaEventRecord(pc.begin, s);
-    cudaError_t e = hr_launch_jobs(ctx->d_regions, r.work, &job, 1, ctx->d_table, aggregate,
+    hr_work w = r.work;
+    w.wait_ns = ctx->wait_ns;
+    w.cas_cap = ctx->cas_cap;
+    w.test_flags = ctx->test_flags;
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, aggregate,
                                    hr_check_grid_size(aggregate), s, ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
@@ -291,7 +298,10 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
     ProfiledCall pc{};
     if (ctx->profile) pc = take_events(ctx);
     if (ctx->profile) cudaEventRecord(pc.begin, s);
-    cudaError_t e = hr_launch_jobs(ctx->d_regions, ctx->batch, js.data(), (unsigned)js.size(), ctx->d_table, true,
+    hr_work w = ctx->batch;
+    w.wait_ns = ctx->wait_ns;
+    w.cas_cap = ctx->cas_cap;
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, true,
                                    hr_check_grid_size(true), s, ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
@@ -414,6 +424,15 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     out->geom = hr_make_geom(r.desc.block_dim, r.desc.warp_size);
     out->kernel = r.kernel;
     out->region = region;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_set_limits(hr_ctx* ctx, uint64_t wait_ns, uint32_t cas_retry_cap, uint32_t test_flags)
+{
+    if (!ctx || wait_ns == 0 || (test_flags & ~HR_TEST_HOLD_STAGE)) return HR_ERR_INVALID;
+    ctx->wait_ns = wait_ns;
+    ctx->cas_cap = cas_retry_cap;
+    ctx->test_flags = test_flags;
     return HR_OK;
 }
 

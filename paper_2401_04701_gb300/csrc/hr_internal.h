@@ -98,8 +98,14 @@ struct hr_work {
     unsigned max_waves;
     unsigned max_intervals;
     unsigned max_jobs;
-    unsigned pad;
+    unsigned cas_cap;                // CAS retries before HR_ERR_CONTENTION
+    unsigned long long wait_ns;      // bound of every device-side wait
+    unsigned test_flags;             // HR_TEST_* hooks (tests only)
+    unsigned pad2;
 };
+
+constexpr unsigned long long HR_DEFAULT_WAIT_NS = 4000000000ull;  // 4 s
+constexpr unsigned HR_DEFAULT_CAS_CAP = 4096;
 
 // bytes of an hr_work scratch block for the given capacities (256-B aligned parts)
 inline size_t hr_work_bytes(unsigned max_jobs, unsigned max_intervals, unsigned max_waves)
@@ -131,6 +137,9 @@ inline hr_work hr_work_at(void* mem, unsigned max_jobs, unsigned max_intervals, 
     w.max_waves = max_waves;
     w.max_intervals = max_intervals;
     w.max_jobs = max_jobs;
+    w.cas_cap = HR_DEFAULT_CAS_CAP;
+    w.wait_ns = HR_DEFAULT_WAIT_NS;
+    w.test_flags = 0;
     return w;
 }
 

@@ -27,7 +27,6 @@
 
 namespace {
 
-constexpr unsigned long long HR_WAIT_NS = 4000000000ull;  // bounded wait: 4 s
 
 template <unsigned CAP>
 struct JobParams {
@@ -267,6 +266,10 @@ __device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
     const unsigned n_st = (unsigned)(tot >> 32);
     for (unsigned i = threadIdx.x; i < n_st; i += blockDim.x)
         if (i > 0) w.stages[i].dep_need = (w.stages[i].item_begin - w.stages[i - 1].item_begin) * HR_CONSUMERS;
+    __syncthreads();
+    // test hook: stage 1 waits for one completion more than stage 0 can give,
+    // so its bounded wait must run out and report HR_ERR_TIMEOUT
+    if (threadIdx.x == 0 && (w.test_flags & HR_TEST_HOLD_STAGE) && n_st > 1) w.stages[1].dep_need += 1;
     if (threadIdx.x == 0) {
         w.stages[n_st] = hr_stage{(unsigned)tot, 0u, HR_STAGE_RECORDS, 0u, HR_NO_DEP, 0u, 0u, 0u};
         if (nw > 0 && w.wave_key[jb.wave_begin] < rg.last_key) hr_set_error(&rg.error, HR_ERR_ORDER);
@@ -429,15 +432,16 @@ __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Bounded mbarrier wait: gives up (and raises the abort flag) after HR_WAIT_NS
+// Bounded mbarrier wait: gives up (and raises the abort flag) after wait_ns
 // or when another CTA aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* abort_flag, unsigned* err)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* abort_flag, unsigned* err,
+                                          unsigned long long wait_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
         if (*(volatile unsigned*)abort_flag) return false;
-        if (globaltimer() - t0 > HR_WAIT_NS) {
+        if (globaltimer() - t0 > wait_ns) {
             atomicExch(abort_flag, 1u);
             hr_set_error(err, HR_ERR_TIMEOUT);
             return false;
@@ -447,13 +451,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
 }
 
 // Bounded wait until a stage's completion count reaches `need`.
-__device__ __forceinline__ bool stage_wait(const unsigned* done, unsigned need, unsigned* abort_flag, unsigned* err)
+__device__ __forceinline__ bool stage_wait(const unsigned* done, unsigned need, unsigned* abort_flag, unsigned* err,
+                                           unsigned long long wait_ns)
 {
     const unsigned long long t0 = globaltimer();
     unsigned ns = 64;
     while (ld_acquire_u32(done) < need) {
         if (*(volatile unsigned*)abort_flag) return false;
-        if (globaltimer() - t0 > HR_WAIT_NS) {
+        if (globaltimer() - t0 > wait_ns) {
             atomicExch(abort_flag, 1u);
             hr_set_error(err, HR_ERR_TIMEOUT);
             return false;
@@ -495,11 +500,11 @@ __device__ __noinline__ unsigned long long fold_group(unsigned long long o, unsi
 __device__ __noinline__ unsigned retry_cas(unsigned long long* p, unsigned long long seen, unsigned tid, unsigned op,
                                            unsigned grp, const Acc* acc, unsigned bc, unsigned wc, unsigned ktag,
                                            const hr_geom& g, const unsigned char* table, unsigned* raced,
-                                           unsigned* who, bool* ok)
+                                           unsigned* who, bool* ok, unsigned cap)
 {
     const unsigned lane = threadIdx.x & 31;
     unsigned attempts = 0;
-    for (int tries = 0; tries < HR_CAS_RETRY_CAP; ++tries) {
+    for (unsigned tries = 0; tries < cap; ++tries) {
         const unsigned long long o = seen;
         *raced = 0;
         *who = lane;
@@ -533,7 +538,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (it >= HR_RING &&
-            !mbar_wait(&s_empty[b], ((it / HR_RING) - 1) & 1u, &w.ctl->abort, &regions[region].error)) {
+            !mbar_wait(&s_empty[b], ((it / HR_RING) - 1) & 1u, &w.ctl->abort, &regions[region].error, w.wait_ns)) {
             s_info[b].valid = 0;
             mbar_arrive(&s_full[b]);
             return;
@@ -650,7 +655,9 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
 
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
-        if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, &region->error)) break;
+        if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, region ? &region->error : &regions[0].error,
+                       w.wait_ns))
+            break;
         const TileInfo info = s_info[b];
         if (!info.valid) break;
         const bool records = info.type == HR_STAGE_RECORDS && !info.skip;
@@ -687,7 +694,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
         if (info.type == HR_STAGE_CLEAR && !info.skip) {
             if (!ready) {
                 bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error);
+                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error, w.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 __syncwarp();
                 if (!ok) break;
@@ -782,7 +789,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
                         asm volatile("{\n\t.reg .b64 t;\n\tld.relaxed.gpu.global.u64 t, [%0];\n\t}" ::"l"(shadow + word[k])
                                      : "memory");
                 bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error);
+                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error, w.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 __syncwarp();
                 if (!ok) break;
@@ -822,7 +829,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
                 if (!done) {
                     c_retry++;
                     c_cas += retry_cas(shadow + word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc, wc, ktag,
-                                       g, s_table, &raced[k], &who[k], &done);
+                                       g, s_table, &raced[k], &who[k], &done, w.cas_cap);
                     if (!done) hr_set_error(&region->error, HR_ERR_CONTENTION);
                 }
                 if (done && raced[k]) {

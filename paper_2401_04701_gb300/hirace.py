@@ -83,6 +83,8 @@ def load_library():
     lib.hr_counters.argtypes = [P, u32, ctypes.POINTER(u64 * 4)]
     lib.hr_reset.argtypes = [P, u32, P]
     lib.hr_destroy.argtypes = [P]
+    lib.hr_set_limits.argtypes = [P, u64, u32, u32]
+    lib.hr_set_limits.restype = i32
     lib.hr_profile_enable.argtypes = [P, i32]
     lib.hr_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(u64), ctypes.POINTER(u64)]
@@ -238,6 +240,10 @@ class Checker:
         v = HrView()
         self._check(self._lib.hr_device_view(self._ctx, region, ctypes.byref(v)), "hr_device_view")
         return v
+
+    def set_limits(self, wait_ns: int = 4_000_000_000, cas_retry_cap: int = 4096, test_flags: int = 0):
+        """Bounds of device waits (ns) and CAS retries; test_flags=1 holds stage 1 (tests only)."""
+        self._check(self._lib.hr_set_limits(self._ctx, wait_ns, cas_retry_cap, test_flags), "hr_set_limits")
 
     def profile(self, on: bool = True):
         self._check(self._lib.hr_profile_enable(self._ctx, int(on)), "hr_profile_enable")

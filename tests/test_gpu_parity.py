@@ -234,3 +234,43 @@ def test_powerlaw_push_full_size_sampled(oracle_mod, hr):
     assert got == want
     # every kernel's racy words include the injected words whose write meets another thread
     assert len(want) > 0
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers(oracle_mod, hr):
+    """A stage dependency that nothing satisfies: the wait runs out after its
+    bound, the region reports HR_ERR_TIMEOUT, and the next check is exact."""
+    import time
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 8), inject=True, n_blocks=4)
+    want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, 256))
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=256)]) as ck:
+        ck.set_limits(wait_ns=200_000_000, test_flags=1)
+        t0 = time.perf_counter()
+        ck.check_trace(0, to_dev(tr))
+        _, status, _, _ = ck.report(0)
+        took = time.perf_counter() - t0
+        assert hr.STATUS[status] == "HR_ERR_TIMEOUT"
+        assert took < 5.0
+        ck.set_limits()
+        ck.reset(0)
+        ck.check_trace(0, to_dev(tr))
+        races, status, _, _ = ck.report(0)
+        assert status == hr.HR_OK and hr.race_keys(races) == want
+
+
+def test_cas_retry_cap_reports_contention(hr):
+    """Zero retries allowed and 64K threads of 256 blocks writing one word in one
+    wave: some CAS loses and the region reports HR_ERR_CONTENTION."""
+    n = 1 << 16
+    tr = np.zeros(n, tg.RECORD)
+    tr["tid"] = np.arange(n)
+    tr["op"] = tg.OP_W
+    with hr.Checker([dict(n_words=1, block_dim=256)]) as ck:
+        ck.set_limits(cas_retry_cap=0)
+        ck.check_trace(0, to_dev(tr), aggregate=False)
+        _, status, _, _ = ck.report(0)
+        assert hr.STATUS[status] == "HR_ERR_CONTENTION"
+        ck.set_limits()
+        ck.reset(0)
+        ck.check_trace(0, to_dev(tr), aggregate=False)
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK and n_total == 1
