@@ -116,6 +116,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value, device=None):
+    """The largest per-rank value (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank_per_step, steps, max_ms):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank_per_step * steps / (max_ms / 1e3)
+
+
 def make_workload(n_blocks=1024):
     from paper_2401_04701_gb300 import tracegen as tg
     trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True, n_blocks=n_blocks)
@@ -403,10 +419,7 @@ def run_gpu(args, rank, world, local_rank):
     _, status, _, _ = ck.report(0)
     if status != hirace.HR_OK:
         raise SystemExit("timed steps ended with %s" % hirace.STATUS[status])
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
 
     # end to end through the C-ABI from pinned host memory: H2D of the trace,
     # reset, check, D2H of the race records
@@ -426,7 +439,7 @@ def run_gpu(args, rank, world, local_rank):
     if rank != 0:
         ck.close()
         return
-    value = world * n_acc * args.steps / (ms / 1e3)
+    value = job_rate(world, n_acc, args.steps, ms)
     p_hbm, peak_kind = peaks()
     alg_bytes = n_acc * ALG_BYTES_PER_ACCESS + n_sync * ALG_BYTES_PER_SYNC
     check_ms = prof["check_ms"] / max(1, prof["calls"])
