@@ -383,6 +383,8 @@ def run_gpu(args, rank, world, local_rank):
     ring = 1 << 22
     ck = hirace.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])], report_capacity=ring)
 
+    # the autotuner picks the kernel variant (tile shape, aggregation) on this workload
+    best, tune_ms = ck.autotune(0, d_trace)
     # correctness gate: one check vs the injected set
     ck.check_trace(0, d_trace)
     races, status, n_total, _ = ck.report(0)
@@ -459,13 +461,15 @@ def run_gpu(args, rank, world, local_rank):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
                      "frac": achieved / p_hbm, "traffic": measured_traffic() if args.blocks == 1024 else None,
-                     "kernel": "hr_check_kernel<true>",
+                     "kernel": "hr_check_kernel variant %d" % best,
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
                 "d2h_bytes_per_step": int(d2h // max(1, e2e_steps))},
         "fsm_counters": {k: int(v) for k, v in counters.items()},
         "gpu_launches": int(prof["launches"]),
+        "autotune": {"chosen": best, "variant": dict(hirace.variants())[best],
+                     "ms_per_variant": [round(t, 4) for t in tune_ms]},
         "clocks": clk,
     }
     if cpu:

@@ -236,6 +236,24 @@ hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_t n_words, 
 hr_status hr_destroy(hr_ctx* ctx);
 
 /*
+ * Kernel variants and the autotuner (no paper counterpart; the tile schedule
+ * of the checker).  A variant fixes the consumer warps per CTA, the records
+ * each consumer lane takes per tile and whether lanes on the same word are
+ * aggregated; even ids aggregate and the odd id after each is the same shape
+ * without aggregation.  hr_autotune checks the given trace on `region` with
+ * every variant (reset before each run, a warm-up then a timed run on
+ * `stream`, synchronous), keeps the fastest for this context's later checks,
+ * writes it to *best and the per-variant milliseconds to ms[0..ms_cap), and
+ * leaves the region reset.  Returns the region's error if the trace is bad.
+ */
+uint32_t hr_variant_count(void);
+hr_status hr_variant_desc(uint32_t id, uint32_t* aggregate, uint32_t* records_per_lane, uint32_t* consumer_warps);
+hr_status hr_set_variant(hr_ctx* ctx, uint32_t id);
+hr_status hr_get_variant(hr_ctx* ctx, uint32_t* id);
+hr_status hr_autotune(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n, hr_stream_t stream,
+                      uint32_t* best, float* ms, uint32_t ms_cap);
+
+/*
  * hr_set_limits - bounds of the device-side waits and retries of this
  * context's later checks (Sec. III-A: checking stops with a report rather than
  * running on).  wait_ns (> 0, default 4e9) bounds every wait of a CTA on the

@@ -70,6 +70,7 @@ struct hr_ctx {
     unsigned long long wait_ns = HR_DEFAULT_WAIT_NS;
     unsigned cas_cap = HR_DEFAULT_CAS_CAP;
     unsigned test_flags = 0;
+    unsigned variant = 0;              // kernel variant of later checks (hr_set_variant / hr_autotune)
     cudaStream_t copies = nullptr;     // non-blocking stream for report copies (never waits on user streams)
     void* batch_mem = nullptr;         // scratch of hr_check_batch (allocated on first use)
     hr_work batch{};
@@ -116,6 +117,7 @@ static void free_ctx(hr_ctx* c)
 }
 
 static bool valid_region(hr_ctx* ctx, uint32_t region) { return ctx && region < ctx->regions.size(); }
+static hr_status fetch_region(hr_ctx* ctx, uint32_t region, hr_region_dev* out);
 
 extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
                              uint64_t report_capacity, hr_stream_t stream)
@@ -205,8 +207,9 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
     w.test_flags = ctx->test_flags;
-    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, aggregate,
-                                   hr_check_grid_size(aggregate), s, ctx->profile ? pc.mid : nullptr);
+    const unsigned variant = aggregate ? ctx->variant : (ctx->variant | 1u);  // odd ids do not aggregate
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, variant, s,
+                                   ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
         pc.launches = HR_LAUNCHES_PER_CHECK;
@@ -301,8 +304,8 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
     hr_work w = ctx->batch;
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
-    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, true,
-                                   hr_check_grid_size(true), s, ctx->profile ? pc.mid : nullptr);
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, ctx->variant, s,
+                                   ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
         pc.launches = HR_LAUNCHES_PER_CHECK;
@@ -425,6 +428,75 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     out->kernel = r.kernel;
     out->region = region;
     return HR_OK;
+}
+
+extern "C" uint32_t hr_variant_count(void) { return HR_N_VARIANTS; }
+
+extern "C" hr_status hr_variant_desc(uint32_t id, uint32_t* aggregate, uint32_t* records_per_lane,
+                                     uint32_t* consumer_warps)
+{
+    if (id >= HR_N_VARIANTS) return HR_ERR_INVALID;
+    if (aggregate) *aggregate = (uint32_t)HR_VARIANTS[id].aggregate;
+    if (records_per_lane) *records_per_lane = (uint32_t)HR_VARIANTS[id].rpl;
+    if (consumer_warps) *consumer_warps = (uint32_t)HR_VARIANTS[id].consumers;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_set_variant(hr_ctx* ctx, uint32_t id)
+{
+    if (!ctx || id >= HR_N_VARIANTS) return HR_ERR_INVALID;
+    ctx->variant = id;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_get_variant(hr_ctx* ctx, uint32_t* id)
+{
+    if (!ctx || !id) return HR_ERR_INVALID;
+    *id = ctx->variant;
+    return HR_OK;
+}
+
+extern "C" hr_status hr_autotune(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
+                                 hr_stream_t stream, uint32_t* best, float* ms, uint32_t ms_cap)
+{
+    if (!valid_region(ctx, region) || !d_trace || n == 0 || (ms_cap > 0 && !ms)) return HR_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const unsigned saved = ctx->variant;
+    const bool saved_profile = ctx->profile;
+    ctx->profile = false;
+    float best_ms = 0.0f;
+    unsigned best_v = saved;
+    hr_status st = HR_OK;
+    for (unsigned v = 0; v < HR_N_VARIANTS && e == cudaSuccess && st == HR_OK; ++v) {
+        ctx->variant = v;
+        float t = 0.0f;
+        for (int rep = 0; rep < 2 && st == HR_OK && e == cudaSuccess; ++rep) {  // warm-up, then timed
+            st = hr_reset(ctx, region, stream);
+            if (st == HR_OK) e = cudaEventRecord(a, s);
+            if (st == HR_OK && e == cudaSuccess) st = check_common(ctx, region, d_trace, n, 0, stream, true);
+            if (st == HR_OK && e == cudaSuccess) e = cudaEventRecord(b, s);
+            if (st == HR_OK && e == cudaSuccess) e = cudaEventSynchronize(b);
+            if (st == HR_OK && e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+        }
+        hr_region_dev h;
+        if (st == HR_OK && e == cudaSuccess) st = fetch_region(ctx, region, &h);
+        if (st == HR_OK && h.error != 0) st = (hr_status)h.error;  // the trace itself is bad
+        if (v < ms_cap) ms[v] = t;
+        if (st == HR_OK && e == cudaSuccess && (v == 0 || t < best_ms)) {
+            best_ms = t;
+            best_v = v;
+        }
+    }
+    ctx->profile = saved_profile;
+    ctx->variant = (st == HR_OK && e == cudaSuccess) ? best_v : saved;
+    if (best) *best = ctx->variant;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (st == HR_OK) st = hr_reset(ctx, region, stream);
+    return st != HR_OK ? st : cuda_status(e);
 }
 
 extern "C" hr_status hr_set_limits(hr_ctx* ctx, uint64_t wait_ns, uint32_t cas_retry_cap, uint32_t test_flags)

@@ -98,10 +98,11 @@ struct hr_work {
     unsigned max_waves;
     unsigned max_intervals;
     unsigned max_jobs;
+    unsigned tile;                   // records per work item (set per kernel variant)
+    unsigned consumers;              // per-warp completions per work item
     unsigned cas_cap;                // CAS retries before HR_ERR_CONTENTION
     unsigned long long wait_ns;      // bound of every device-side wait
     unsigned test_flags;             // HR_TEST_* hooks (tests only)
-    unsigned pad2;
 };
 
 constexpr unsigned long long HR_DEFAULT_WAIT_NS = 4000000000ull;  // 4 s
@@ -145,10 +146,17 @@ inline hr_work hr_work_at(void* mem, unsigned max_jobs, unsigned max_intervals, 
 
 constexpr unsigned HR_MAX_BATCH = 512;  // jobs per batched launch
 
-constexpr int HR_CONSUMERS = 8;                          // consumer warps per CTA
-constexpr int HR_THREADS = (HR_CONSUMERS + 1) * 32;      // + one producer warp
-constexpr int HR_RPL = 4;                                // records per consumer lane per tile
-constexpr int HR_TILE = HR_CONSUMERS * 32 * HR_RPL;      // records per tile (one wave per tile)
+// Kernel variants (chosen by hr_set_variant / hr_autotune): consumer warps per
+// CTA, records per consumer lane, warp aggregation.  Even ids aggregate; the
+// odd id after each is the same shape without aggregation.
+struct hr_variant {
+    int aggregate;
+    int rpl;         // records per consumer lane per tile
+    int consumers;   // consumer warps per CTA (plus one producer warp)
+};
+constexpr hr_variant HR_VARIANTS[] = {{1, 4, 8}, {0, 4, 8}, {1, 2, 8}, {0, 2, 8}, {1, 8, 4}, {0, 8, 4}};
+constexpr unsigned HR_N_VARIANTS = sizeof(HR_VARIANTS) / sizeof(HR_VARIANTS[0]);
+constexpr unsigned hr_variant_tile(unsigned v) { return HR_VARIANTS[v].consumers * 32u * HR_VARIANTS[v].rpl; }
 #ifndef HR_RING_DEPTH
 #define HR_RING_DEPTH 2
 #endif
@@ -169,11 +177,11 @@ constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;
 // Check n_jobs jobs (1..HR_MAX_BATCH) on the regions of d_regions with the
 // scratch w.  Jobs must name distinct regions and hold n > 0 records.
 cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_jobd* jobs, unsigned n_jobs,
-                           const unsigned char* d_table, bool aggregate, int grid, cudaStream_t stream,
+                           const unsigned char* d_table, unsigned variant, cudaStream_t stream,
                            cudaEvent_t before_check);
 // interval size and count for a job of n records when it may use up to budget intervals
 void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int);
-int hr_check_grid_size(bool aggregate);
+int hr_check_grid_size(unsigned variant);
 constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
 cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long n_words,

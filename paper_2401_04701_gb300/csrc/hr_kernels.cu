@@ -224,7 +224,7 @@ __device__ __forceinline__ void wave_plan(const hr_work& w, const hr_jobd& jb, c
     *clear = (L > 0 || rg.used) && (kern >> 3) != (prev >> 3);
     const unsigned long long end = L + 1 < jb.n_waves ? w.wave_start[g + 1] : jb.n;
     w.wave_end[g] = end;
-    *rec_items = (unsigned)((end - w.wave_start[g] + HR_TILE - 1) / HR_TILE);
+    *rec_items = (unsigned)((end - w.wave_start[g] + w.tile - 1) / w.tile);
     *clr_items = *clear ? (unsigned)((rg.n_words + HR_CLEAR_WORDS - 1) / HR_CLEAR_WORDS) : 0u;
 }
 
@@ -265,7 +265,7 @@ __device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
     // dependency need = items of the previous stage x per-warp completions
     const unsigned n_st = (unsigned)(tot >> 32);
     for (unsigned i = threadIdx.x; i < n_st; i += blockDim.x)
-        if (i > 0) w.stages[i].dep_need = (w.stages[i].item_begin - w.stages[i - 1].item_begin) * HR_CONSUMERS;
+        if (i > 0) w.stages[i].dep_need = (w.stages[i].item_begin - w.stages[i - 1].item_begin) * w.consumers;
     __syncthreads();
     // test hook: stage 1 waits for one completion more than stage 0 can give,
     // so its bounded wait must run out and report HR_ERR_TIMEOUT
@@ -319,13 +319,13 @@ __device__ void stages_many_jobs(hr_work& w, hr_region_dev* regions)
             unsigned s = base_s + (unsigned)(pre >> 32), it = base_i + (unsigned)pre;
             const unsigned g = jb.wave_begin + L;
             if (clear) {
-                w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, last, last_items * HR_CONSUMERS, j, 0u};
+                w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, last, last_items * w.consumers, j, 0u};
                 last = s;
                 last_items = ci;
                 s++;
                 it += ci;
             }
-            w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, last, last_items * HR_CONSUMERS, j, 0u};
+            w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, last, last_items * w.consumers, j, 0u};
             last = s;
             last_items = ri;
         }
@@ -375,9 +375,15 @@ struct Acc {
     unsigned op;
 };
 
-constexpr size_t SMEM_REC = (size_t)HR_RING * HR_TILE * sizeof(uint4);
-constexpr size_t SMEM_ACC = (size_t)HR_CONSUMERS * HR_RPL * 32 * sizeof(Acc);
-constexpr size_t SMEM_BYTES = SMEM_REC + 2048 + SMEM_ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8;
+template <int RPL, int CONS>
+struct Shape {
+    static constexpr int TILE = CONS * 32 * RPL;
+    static constexpr int THREADS = (CONS + 1) * 32;
+    static constexpr size_t REC = (size_t)HR_RING * TILE * sizeof(uint4);
+    static constexpr size_t ACC = (size_t)CONS * RPL * 32 * sizeof(Acc);
+    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8;
+    static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -525,6 +531,7 @@ __device__ __noinline__ unsigned retry_cas(unsigned long long* p, unsigned long 
     return attempts;
 }
 
+template <int TILE>
 __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, TileInfo* s_info, uint64_t* s_full,
                               uint64_t* s_empty)
 {
@@ -585,24 +592,30 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
         info.skip = skip;
         info.key = key;
         info.kb = kb;
-        info.rb = w_start + (unsigned long long)info.item * HR_TILE;
-        info.re = min(info.rb + HR_TILE, w_end);
+        info.rb = w_start + (unsigned long long)info.item * TILE;
+        info.re = min(info.rb + TILE, w_end);
         s_info[b] = info;
         if (type == HR_STAGE_RECORDS && !info.skip) {
             const uint32_t bytes = (uint32_t)(info.re - info.rb) * (uint32_t)sizeof(hr_record);
             mbar_arrive_tx(&s_full[b], bytes);
-            bulk_g2s(s_rec + (size_t)b * HR_TILE, trace + info.rb, bytes, &s_full[b], pol);
+            bulk_g2s(s_rec + (size_t)b * TILE, trace + info.rb, bytes, &s_full[b], pol);
         } else {
             mbar_arrive(&s_full[b]);
         }
     }
 }
 
-template <bool AGG>
-__global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_region_dev* __restrict__ regions,
+template <bool AGG, int HR_RPL, int HR_CONSUMERS>
+__global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR_RPL, HR_CONSUMERS>::MIN_CTAS)
+    hr_check_kernel(hr_region_dev* __restrict__ regions,
                                                                  hr_work w,
                                                                  const unsigned char* __restrict__ gtable)
 {
+    using S = Shape<HR_RPL, HR_CONSUMERS>;
+    constexpr int HR_TILE = S::TILE;
+    constexpr int HR_THREADS = S::THREADS;
+    constexpr size_t SMEM_REC = S::REC;
+    constexpr size_t SMEM_ACC = S::ACC;
     extern __shared__ __align__(128) unsigned char smem[];
     uint4* s_rec = reinterpret_cast<uint4*>(smem);
     unsigned char* s_table = smem + SMEM_REC;
@@ -624,7 +637,7 @@ __global__ void __launch_bounds__(HR_THREADS, HR_MIN_CTAS) hr_check_kernel(hr_re
     __syncthreads();
 
     if (wid == HR_CONSUMERS) {
-        if (lane == 0) producer_loop(w, regions, s_rec, s_info, s_full, s_empty);
+        if (lane == 0) producer_loop<HR_TILE>(w, regions, s_rec, s_info, s_full, s_empty);
         return;
     }
 
@@ -870,26 +883,44 @@ __global__ void hr_reconfigure_state(hr_region_dev* region, unsigned long long n
     region->geom = geom;
 }
 
-int g_grid[2] = {0, 0};
+int g_grid[HR_N_VARIANTS] = {};
 
-}  // namespace
-
-int hr_check_grid_size(bool aggregate)
+template <bool AGG, int RPL, int CONS>
+int grid_for()
 {
-    int& cached = g_grid[aggregate ? 1 : 0];
-    if (cached) return cached;
+    using S = Shape<RPL, CONS>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (aggregate) {
-        cudaFuncSetAttribute(hr_check_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<true>, HR_THREADS, SMEM_BYTES);
-    } else {
-        cudaFuncSetAttribute(hr_check_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<false>, HR_THREADS, SMEM_BYTES);
-    }
+    cudaFuncSetAttribute(hr_check_kernel<AGG, RPL, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<AGG, RPL, CONS>, S::THREADS, S::BYTES);
     if (per_sm < 1) per_sm = 1;
-    cached = sms * per_sm;
+    return sms * per_sm;
+}
+
+template <bool AGG, int RPL, int CONS>
+void launch_variant(int grid, hr_region_dev* d_regions, const hr_work& w, const unsigned char* d_table,
+                    cudaStream_t stream)
+{
+    using S = Shape<RPL, CONS>;
+    hr_check_kernel<AGG, RPL, CONS><<<grid, S::THREADS, S::BYTES, stream>>>(d_regions, w, d_table);
+}
+
+}  // namespace
+
+int hr_check_grid_size(unsigned variant)
+{
+    if (variant >= HR_N_VARIANTS) variant = 0;
+    int& cached = g_grid[variant];
+    if (cached) return cached;
+    switch (variant) {
+    case 0: cached = grid_for<true, 4, 8>(); break;
+    case 1: cached = grid_for<false, 4, 8>(); break;
+    case 2: cached = grid_for<true, 2, 8>(); break;
+    case 3: cached = grid_for<false, 2, 8>(); break;
+    case 4: cached = grid_for<true, 8, 4>(); break;
+    default: cached = grid_for<false, 8, 4>(); break;
+    }
     return cached;
 }
 
@@ -913,10 +944,15 @@ static void launch_prepass(const JobParams<CAP>& P, unsigned total_int, hr_regio
     hr_build_stages<<<1, 1024, 0, stream>>>(w, d_regions);
 }
 
-cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_jobd* jobs, unsigned n_jobs,
-                           const unsigned char* d_table, bool aggregate, int grid, cudaStream_t stream,
+cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const hr_jobd* jobs, unsigned n_jobs,
+                           const unsigned char* d_table, unsigned variant, cudaStream_t stream,
                            cudaEvent_t before_check)
 {
+    if (variant >= HR_N_VARIANTS) return cudaErrorInvalidValue;
+    hr_work w = w_in;
+    w.tile = hr_variant_tile(variant);
+    w.consumers = (unsigned)HR_VARIANTS[variant].consumers;
+    const int grid = hr_check_grid_size(variant);
     if (n_jobs == 0 || n_jobs > HR_MAX_BATCH || n_jobs > w.max_jobs) return cudaErrorInvalidValue;
     const unsigned total_int = jobs[n_jobs - 1].int_begin + jobs[n_jobs - 1].n_int;
     if (total_int > w.max_intervals) return cudaErrorInvalidValue;
@@ -932,10 +968,14 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_
         launch_prepass(P, total_int, d_regions, w, stream);
     }
     if (before_check) cudaEventRecord(before_check, stream);
-    if (aggregate)
-        hr_check_kernel<true><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
-    else
-        hr_check_kernel<false><<<grid, HR_THREADS, SMEM_BYTES, stream>>>(d_regions, w, d_table);
+    switch (variant) {
+    case 0: launch_variant<true, 4, 8>(grid, d_regions, w, d_table, stream); break;
+    case 1: launch_variant<false, 4, 8>(grid, d_regions, w, d_table, stream); break;
+    case 2: launch_variant<true, 2, 8>(grid, d_regions, w, d_table, stream); break;
+    case 3: launch_variant<false, 2, 8>(grid, d_regions, w, d_table, stream); break;
+    case 4: launch_variant<true, 8, 4>(grid, d_regions, w, d_table, stream); break;
+    default: launch_variant<false, 8, 4>(grid, d_regions, w, d_table, stream); break;
+    }
     return cudaGetLastError();
 }
 

@@ -115,7 +115,7 @@ extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n
         job.n = n;
         job.region = 0;  // the region array is the single struct above
         hr_plan_intervals(n, HR_MAX_INTERVALS, &job.G, &job.n_int);
-        e = hr_launch_jobs(region, w, &job, 1, base + OFF_TABLE, true, hr_check_grid_size(true), s, nullptr);
+        e = hr_launch_jobs(region, w, &job, 1, base + OFF_TABLE, 0u, s, nullptr);
     }
     if (e == cudaSuccess) {
         hr_noalloc_end<<<1, 1, 0, s>>>(region, d_result);

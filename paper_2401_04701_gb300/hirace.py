@@ -83,6 +83,15 @@ def load_library():
     lib.hr_counters.argtypes = [P, u32, ctypes.POINTER(u64 * 4)]
     lib.hr_reset.argtypes = [P, u32, P]
     lib.hr_destroy.argtypes = [P]
+    lib.hr_variant_count.restype = u32
+    lib.hr_variant_desc.argtypes = [u32, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.hr_variant_desc.restype = i32
+    lib.hr_set_variant.argtypes = [P, u32]
+    lib.hr_set_variant.restype = i32
+    lib.hr_get_variant.argtypes = [P, ctypes.POINTER(u32)]
+    lib.hr_get_variant.restype = i32
+    lib.hr_autotune.argtypes = [P, u32, P, u64, P, ctypes.POINTER(u32), ctypes.POINTER(ctypes.c_float), u32]
+    lib.hr_autotune.restype = i32
     lib.hr_set_limits.argtypes = [P, u64, u32, u32]
     lib.hr_set_limits.restype = i32
     lib.hr_profile_enable.argtypes = [P, i32]
@@ -118,6 +127,17 @@ def fsm_table():
     if rc:
         raise HiRaceError(rc)
     return out, int(n.value)
+
+
+def variants():
+    """[(id, dict(aggregate, records_per_lane, consumer_warps))] of the checker kernel."""
+    lib = load_library()
+    out = []
+    for i in range(lib.hr_variant_count()):
+        a, r, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        lib.hr_variant_desc(i, ctypes.byref(a), ctypes.byref(r), ctypes.byref(c))
+        out.append((i, dict(aggregate=bool(a.value), records_per_lane=r.value, consumer_warps=c.value)))
+    return out
 
 
 def state_name(state: int) -> str:
@@ -240,6 +260,43 @@ class Checker:
         v = HrView()
         self._check(self._lib.hr_device_view(self._ctx, region, ctypes.byref(v)), "hr_device_view")
         return v
+
+    def set_variant(self, variant: int):
+        self._check(self._lib.hr_set_variant(self._ctx, variant), "hr_set_variant")
+
+    def variant(self) -> int:
+        v = ctypes.c_uint32()
+        self._check(self._lib.hr_get_variant(self._ctx, ctypes.byref(v)), "hr_get_variant")
+        return v.value
+
+    def autotune(self, region: int, trace, stream=None):
+        """Time every kernel variant on this trace, keep the fastest; returns (best, [ms...])."""
+        ptr, n = _ptr_and_count(trace)
+        nv = self._lib.hr_variant_count()
+        ms = (ctypes.c_float * nv)()
+        best = ctypes.c_uint32()
+        self._check(self._lib.hr_autotune(self._ctx, region, ptr, n, _stream_handle(stream), ctypes.byref(best), ms,
+                                          nv), "hr_autotune")
+        return best.value, list(ms)
+
+    def autotune_cached(self, region: int, trace, key: str, stream=None):
+        """Autotune once per workload key; the choice is kept in the JSON file named
+        by $HIRACE_TUNE_CACHE (no file: tune every time)."""
+        import json
+        path = os.environ.get("HIRACE_TUNE_CACHE")
+        cache = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                cache = json.load(f)
+        if key in cache:
+            self.set_variant(int(cache[key]))
+            return int(cache[key]), None
+        best, ms = self.autotune(region, trace, stream)
+        if path:
+            cache[key] = best
+            with open(path, "w") as f:
+                json.dump(cache, f, indent=1)
+        return best, ms
 
     def set_limits(self, wait_ns: int = 4_000_000_000, cas_retry_cap: int = 4096, test_flags: int = 0):
         """Bounds of device waits (ns) and CAS retries; test_flags=1 holds stage 1 (tests only)."""

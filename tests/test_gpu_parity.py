@@ -274,3 +274,42 @@ def test_cas_retry_cap_reports_contention(hr):
         ck.check_trace(0, to_dev(tr), aggregate=False)
         races, status, n_total, _ = ck.report(0)
         assert status == hr.HR_OK and n_total == 1
+
+
+@pytest.fixture(scope="module")
+def variant_cases():
+    cases = []
+    g = C.load_golden("listing2_block_sync")
+    cases.append((C.golden_trace(g), g["n_words"], g["block_dim"], g["warp_size"]))
+    ex = C.exhaustive_cases(3, C.PHASES4)
+    cases.append((C.combined_trace(ex, C.PHASES4), len(ex), C.TOY_BLOCK_DIM, C.TOY_WARP))
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 9), inject=True, n_blocks=8)
+    cases.append((tr, info["n_words"], 256, 32))
+    tr, info = tg.gen_powerlaw_push(tg.seed_for(3, 9), log2_vertices=14, sweeps=2)
+    cases.append((tr, info["n_words"], 256, 32))
+    tr, info = tg.gen_tree_reduction(tg.seed_for(1, 9), segments=8, reps=3)
+    cases.append((tr, info["n_words"], 256, 32))
+    return cases
+
+
+def test_every_kernel_variant_matches_oracle(oracle_mod, hr, variant_cases):
+    for v, desc in hr.variants():
+        for tr, nw, bd, ws in variant_cases:
+            with hr.Checker([dict(n_words=nw, block_dim=bd, warp_size=ws)]) as ck:
+                ck.set_variant(v)
+                ck.check_trace(0, to_dev(tr))
+                races, status, n_total, _ = ck.report(0)
+            want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, bd, ws))
+            assert status == hr.HR_OK and hr.race_keys(races) == want, (v, desc)
+
+
+def test_autotune_keeps_the_fastest(oracle_mod, hr):
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 10), inject=True, n_blocks=16)
+    want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, 256))
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=256)]) as ck:
+        d = to_dev(tr)
+        best, ms = ck.autotune(0, d)
+        assert ck.variant() == best and ms[best] == min(ms) and all(t > 0 for t in ms)
+        ck.check_trace(0, d)
+        races, status, _, _ = ck.report(0)
+    assert status == hr.HR_OK and hr.race_keys(races) == want
