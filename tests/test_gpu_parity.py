@@ -109,10 +109,25 @@ def test_global_mix_small(oracle_mod, hr, aggregate):
 
 
 def test_global_mix_full_size(oracle_mod, hr):
-    """The benchmark workload at full size (1024 x 256 threads, 2^26 words, 75.2M records)."""
+    """The benchmark workload at full size (1024 x 256 threads, 2^26 words, 75.2M
+    records) in the configuration bench.py times: the autotuner's variant, and
+    the trace checked as a later kernel launch (rebased kernel ordinal)."""
     tr, info = tg.gen_global_mix(tg.seed_for(2), inject=True)
-    races = assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"])
-    assert len(races) == len(info["injected"]) == 67108
+    bf = oracle_mod.bruteforce(tr, info["block_dim"])
+    want = oracle_mod.race_keys(bf)
+    assert len(want) == len(info["injected"]) == 67108
+    d = to_dev(tr)
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=256)], report_capacity=1 << 22) as ck:
+        best, _ = ck.autotune(0, d)
+        ck.check_trace(0, d)
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK and hr.race_keys(races) == want and n_total == len(want)
+        ck.reset(0)
+        for kb in (3, 4):
+            ck.check_trace(0, d, kernel_base=kb)
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK and n_total == 2 * len(want)
+        assert hr.race_keys(races) == {(kb, w, e) for kb in (3, 4) for (_, w, e) in want}
 
 
 def test_chunked_calls_equal_one_call(oracle_mod, hr):
