@@ -383,8 +383,13 @@ def run_gpu(args, rank, world, local_rank):
     ring = 1 << 22
     ck = hirace.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])], report_capacity=ring)
 
-    # the autotuner picks the kernel variant (tile shape, aggregation) on this workload
-    best, tune_ms = ck.autotune(0, d_trace)
+    # the autotuner picks the kernel variant (tile shape, aggregation) on this workload,
+    # unless --variant pins one (profiling runs, where tuning under a profiler misleads)
+    if args.variant is None:
+        best, tune_ms = ck.autotune(0, d_trace)
+    else:
+        ck.set_variant(args.variant)
+        best, tune_ms = args.variant, None
     # correctness gate: one check vs the injected set
     ck.check_trace(0, d_trace)
     races, status, n_total, _ = ck.report(0)
@@ -469,7 +474,7 @@ def run_gpu(args, rank, world, local_rank):
         "fsm_counters": {k: int(v) for k, v in counters.items()},
         "gpu_launches": int(prof["launches"]),
         "autotune": {"chosen": best, "variant": dict(hirace.variants())[best],
-                     "ms_per_variant": [round(t, 4) for t in tune_ms]},
+                     "ms_per_variant": [round(t, 4) for t in tune_ms] if tune_ms else "pinned by --variant"},
         "clocks": clk,
     }
     if cpu:
@@ -500,6 +505,8 @@ def main():
                     help="random 8-byte load/CAS/store rates over 16..512 MB arrays, then exit")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="pin the checker kernel variant instead of autotuning")
     ap.add_argument("--blocks", type=int, default=1024,
                     help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()
