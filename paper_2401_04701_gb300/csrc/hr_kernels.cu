@@ -262,10 +262,10 @@ __device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
         it += ri;
     }
     __syncthreads();
-    // dependency need = items of the previous stage x per-warp completions
+    // dependency need = items of the previous stage (one completion per item)
     const unsigned n_st = (unsigned)(tot >> 32);
     for (unsigned i = threadIdx.x; i < n_st; i += blockDim.x)
-        if (i > 0) w.stages[i].dep_need = (w.stages[i].item_begin - w.stages[i - 1].item_begin) * w.consumers;
+        if (i > 0) w.stages[i].dep_need = w.stages[i].item_begin - w.stages[i - 1].item_begin;
     __syncthreads();
     // test hook: stage 1 waits for one completion more than stage 0 can give,
     // so its bounded wait must run out and report HR_ERR_TIMEOUT
@@ -319,13 +319,13 @@ __device__ void stages_many_jobs(hr_work& w, hr_region_dev* regions)
             unsigned s = base_s + (unsigned)(pre >> 32), it = base_i + (unsigned)pre;
             const unsigned g = jb.wave_begin + L;
             if (clear) {
-                w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, last, last_items * w.consumers, j, 0u};
+                w.stages[s] = hr_stage{it, g, HR_STAGE_CLEAR, 0u, last, last_items, j, 0u};
                 last = s;
                 last_items = ci;
                 s++;
                 it += ci;
             }
-            w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, last, last_items * w.consumers, j, 0u};
+            w.stages[s] = hr_stage{it, g, HR_STAGE_RECORDS, 0u, last, last_items, j, 0u};
             last = s;
             last_items = ri;
         }
@@ -368,6 +368,7 @@ struct TileInfo {
     unsigned long long kb;           // the job's kernel base (shifted), to rebase record keys
     unsigned stage, type, item, valid;
     unsigned skip, dep, dep_need, region;
+    unsigned ready, pad[3];           // ready: the producer saw the dependency complete
 };
 
 struct Acc {
@@ -381,7 +382,8 @@ struct Shape {
     static constexpr int THREADS = (CONS + 1) * 32;
     static constexpr size_t REC = (size_t)HR_RING * TILE * sizeof(uint4);
     static constexpr size_t ACC = (size_t)CONS * RPL * 32 * sizeof(Acc);
-    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8;
+    // records, FSM table, aggregation scratch, tile infos, full/empty mbarriers, tile-finish counters
+    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 + 2 * HR_RING * 4;
     static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
 };
 
@@ -431,6 +433,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
+}
+
+__device__ __forceinline__ unsigned smem_add_acq_rel(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+    return old;
 }
 
 __device__ __forceinline__ void red_release_add(unsigned* p, unsigned v)
@@ -542,6 +551,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
     const hr_record* trace = nullptr;
     bool have = false, skip = false;
     unsigned pend = 0, pend_end = 0, polls = 0;
+    unsigned known = HR_NO_DEP;  // last dependency seen complete
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (it >= HR_RING &&
@@ -588,6 +598,12 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
         info.item = t - s_begin;
         info.dep = dep;
         info.dep_need = dep_need;
+        // one look at the dependency here spares every consumer warp its own poll
+        info.ready = dep == HR_NO_DEP || dep == known;
+        if (!info.ready && ld_acquire_u32(&w.stages[dep].done) >= dep_need) {
+            info.ready = 1;
+            known = dep;
+        }
         info.region = region;
         info.skip = skip;
         info.key = key;
@@ -623,6 +639,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     TileInfo* s_info = reinterpret_cast<TileInfo*>(smem + SMEM_REC + 2048 + SMEM_ACC);
     uint64_t* s_full = reinterpret_cast<uint64_t*>(s_info + HR_RING);
     uint64_t* s_empty = s_full + HR_RING;
+    unsigned* s_fin = reinterpret_cast<unsigned*>(s_empty + HR_RING);  // [2 * HR_RING]
 
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
@@ -632,6 +649,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             mbar_init(&s_full[b], 1);
             mbar_init(&s_empty[b], HR_CONSUMERS);
         }
+        for (int b = 0; b < 2 * HR_RING; ++b) s_fin[b] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -695,14 +713,14 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
 
         const unsigned s = info.stage;
         const unsigned dep = info.dep;
-        bool ready = dep == HR_NO_DEP || dep == known;
+        bool ready = dep == HR_NO_DEP || dep == known || info.ready;
         if (!ready) {
             unsigned r = 0;
             if (lane == 0) r = ld_acquire_u32(&w.stages[dep].done) >= info.dep_need;
             ready = __shfl_sync(0xffffffffu, r, 0) != 0;
             __syncwarp();
-            if (ready) known = dep;
         }
+        if (ready && dep != HR_NO_DEP) known = dep;
 
         if (info.type == HR_STAGE_CLEAR && !info.skip) {
             if (!ready) {
@@ -853,8 +871,15 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 }
             }
         }
+        // the warp's part of the tile is done; the CTA's last warp to finish it
+        // publishes one completion for the stage (counters indexed by tile number
+        // mod 2*ring never mix two tiles: a warp cannot finish tile it+2*ring
+        // before every warp has finished tile it)
         __syncwarp();
-        if (lane == 0) red_release_add(&w.stages[s].done, 1u);
+        if (lane == 0) {
+            const unsigned old = smem_add_acq_rel(&s_fin[it % (2 * HR_RING)], 1u);
+            if ((old + 1u) % HR_CONSUMERS == 0) red_release_add(&w.stages[s].done, 1u);
+        }
     }
     flush();
 }
