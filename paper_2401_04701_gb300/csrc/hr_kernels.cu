@@ -382,8 +382,10 @@ struct Shape {
     static constexpr int THREADS = (CONS + 1) * 32;
     static constexpr size_t REC = (size_t)HR_RING * TILE * sizeof(uint4);
     static constexpr size_t ACC = (size_t)CONS * RPL * 32 * sizeof(Acc);
-    // records, FSM table, aggregation scratch, tile infos, full/empty mbarriers, tile-finish counters
-    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 + 2 * HR_RING * 4;
+    // records, FSM table, aggregation scratch, tile infos, full/empty mbarriers,
+    // tile-finish counters, per-warp geometry and diagnostics
+    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 +
+                                    2 * HR_RING * 4 + CONS * sizeof(hr_geom) + CONS * 4 * 4;
     static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
 };
 
@@ -484,12 +486,19 @@ __device__ __forceinline__ bool stage_wait(const unsigned* done, unsigned need, 
     return true;
 }
 
+// Result of folding accesses into a shadow value: the new value, 1 + the
+// prior state when the fold entered RACE (else 0), and the lane whose access
+// did it.  Returned by value so the callers' state stays in registers.
+struct Fold {
+    unsigned long long n;
+    unsigned raced, who;
+};
+
 // Fold the accesses of one lane group (lanes in `grp`, in lane order) into o.
-__device__ __noinline__ unsigned long long fold_group(unsigned long long o, unsigned grp, const Acc* acc,
-                                                         unsigned bc, unsigned wc, unsigned ktag,
-                                                         const hr_geom& g, const unsigned char* table,
-                                                         unsigned* raced, unsigned* who)
+__device__ __noinline__ Fold fold_group(unsigned long long o, unsigned grp, const Acc* acc, unsigned bc, unsigned wc,
+                                        unsigned ktag, const hr_geom& g, const unsigned char* table)
 {
+    Fold f{o, 0u, threadIdx.x & 31};
     unsigned last_tid = ~0u, last_op = ~0u;
     while (grp) {
         const unsigned l = __ffs(grp) - 1;
@@ -500,44 +509,52 @@ __device__ __noinline__ unsigned long long fold_group(unsigned long long o, unsi
         last_tid = acc[l].tid;
         last_op = acc[l].op;
         unsigned r = 0;
-        o = hr_fsm_step(o, acc[l].tid, acc[l].op, bc, wc, ktag, g, table, &r);
-        if (r && !*raced) {
-            *raced = r;
-            *who = l;
+        f.n = hr_fsm_step(f.n, acc[l].tid, acc[l].op, bc, wc, ktag, g, table, &r);
+        if (r && !f.raced) {
+            f.raced = r;
+            f.who = l;
         }
     }
-    return o;
+    return f;
 }
+
+// Outcome of the cold CAS path.
+struct Retry {
+    unsigned raced, who;
+    unsigned attempts;  // extra CAS attempts
+    unsigned ok;        // a CAS stuck (or the access needed none)
+};
 
 // Cold path: the first CAS lost a race (or validated a stale speculative
 // load).  Re-fold from the value it returned until a CAS sticks or the retry
-// cap is reached.  Returns the number of extra CAS attempts; *ok tells success.
-__device__ __noinline__ unsigned retry_cas(unsigned long long* p, unsigned long long seen, unsigned tid, unsigned op,
-                                           unsigned grp, const Acc* acc, unsigned bc, unsigned wc, unsigned ktag,
-                                           const hr_geom& g, const unsigned char* table, unsigned* raced,
-                                           unsigned* who, bool* ok, unsigned cap)
+// cap is reached.
+__device__ __noinline__ Retry retry_cas(unsigned long long* p, unsigned long long seen, unsigned tid, unsigned op,
+                                        unsigned grp, const Acc* acc, unsigned bc, unsigned wc, unsigned ktag,
+                                        const hr_geom& g, const unsigned char* table, unsigned cap)
 {
     const unsigned lane = threadIdx.x & 31;
-    unsigned attempts = 0;
+    Retry r{0u, lane, 0u, 0u};
     for (unsigned tries = 0; tries < cap; ++tries) {
         const unsigned long long o = seen;
-        *raced = 0;
-        *who = lane;
-        const unsigned long long n = grp == (1u << lane) ? hr_fsm_step(o, tid, op, bc, wc, ktag, g, table, raced)
-                                                         : fold_group(o, grp, acc, bc, wc, ktag, g, table, raced, who);
-        if (n == o) {
-            *ok = true;
-            return attempts;
+        Fold f{o, 0u, lane};
+        if (grp == (1u << lane))
+            f.n = hr_fsm_step(o, tid, op, bc, wc, ktag, g, table, &f.raced);
+        else
+            f = fold_group(o, grp, acc, bc, wc, ktag, g, table);
+        r.raced = f.raced;
+        r.who = f.who;
+        if (f.n == o) {
+            r.ok = 1;
+            return r;
         }
-        attempts++;
-        seen = atomicCAS(p, o, n);
+        r.attempts++;
+        seen = atomicCAS(p, o, f.n);
         if (seen == o) {
-            *ok = true;
-            return attempts;
+            r.ok = 1;
+            return r;
         }
     }
-    *ok = false;
-    return attempts;
+    return r;
 }
 
 template <int TILE>
@@ -640,6 +657,8 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     uint64_t* s_full = reinterpret_cast<uint64_t*>(s_info + HR_RING);
     uint64_t* s_empty = s_full + HR_RING;
     unsigned* s_fin = reinterpret_cast<unsigned*>(s_empty + HR_RING);  // [2 * HR_RING]
+    hr_geom* s_geom = reinterpret_cast<hr_geom*>(s_fin + 2 * HR_RING);  // [HR_CONSUMERS]
+    unsigned* s_cnt = reinterpret_cast<unsigned*>(s_geom + HR_CONSUMERS);  // [HR_CONSUMERS][4]
 
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
@@ -662,26 +681,38 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     // ---- consumer warp
     unsigned cur = ~0u;  // region of the previous tile
     hr_region_dev* region = nullptr;
-    hr_geom g{};
+    // the region's geometry lives in this warp's shared slot (read per use, not held in registers)
+    const hr_geom& g = s_geom[wid];
     unsigned long long* shadow = nullptr;
     unsigned long long n_words = 0;
     Acc* my_acc = s_acc + (size_t)wid * HR_RPL * 32;
     unsigned known = HR_NO_DEP;  // last dependency this warp has seen complete
-    unsigned long long c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
+    // diagnostics: lane counts summed per tile into this warp's shared counters
+    unsigned* cnt = s_cnt + wid * 4;
+    if (lane < 4) cnt[lane] = 0;
+    __syncwarp();
+    auto count = [&](unsigned acc_n, unsigned cas_n, unsigned retry_n, unsigned merged_n) {
+        unsigned v[4] = {acc_n, cas_n, retry_n, merged_n};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            unsigned x = v[i];
+            if (__any_sync(0xffffffffu, x != 0)) {
+                for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o2);
+                if (lane == 0) cnt[i] += x;
+            }
+        }
+    };
     auto flush = [&]() {
-        for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            c_acc += __shfl_xor_sync(0xffffffffu, c_acc, o2);
-            c_cas += __shfl_xor_sync(0xffffffffu, c_cas, o2);
-            c_retry += __shfl_xor_sync(0xffffffffu, c_retry, o2);
-            c_merged += __shfl_xor_sync(0xffffffffu, c_merged, o2);
-        }
+        __syncwarp();
         if (lane == 0 && region) {
-            if (c_acc) atomicAdd(&region->counters[0], c_acc);
-            if (c_cas) atomicAdd(&region->counters[1], c_cas);
-            if (c_retry) atomicAdd(&region->counters[2], c_retry);
-            if (c_merged) atomicAdd(&region->counters[3], c_merged);
+            if (cnt[0]) atomicAdd(&region->counters[0], (unsigned long long)cnt[0]);
+            if (cnt[1]) atomicAdd(&region->counters[1], (unsigned long long)cnt[1]);
+            if (cnt[2]) atomicAdd(&region->counters[2], (unsigned long long)cnt[2]);
+            if (cnt[3]) atomicAdd(&region->counters[3], (unsigned long long)cnt[3]);
         }
-        c_acc = c_cas = c_retry = c_merged = 0;
+        __syncwarp();
+        if (lane < 4) cnt[lane] = 0;
+        __syncwarp();
     };
 
     for (unsigned it = 0;; ++it) {
@@ -689,50 +720,55 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, region ? &region->error : &regions[0].error,
                        w.wait_ns))
             break;
-        const TileInfo info = s_info[b];
-        if (!info.valid) break;
-        const bool records = info.type == HR_STAGE_RECORDS && !info.skip;
+        // take what the tile needs out of the slot, then release it
+        const TileInfo& ti = s_info[b];
+        if (!ti.valid) break;
+        const unsigned t_type = ti.type, t_skip = ti.skip, t_stage = ti.stage, t_dep = ti.dep;
+        const unsigned t_need = ti.dep_need, t_item = ti.item, t_region = ti.region, t_ready = ti.ready;
+        const unsigned t_n = (unsigned)(ti.re - ti.rb);  // records in this tile (<= HR_TILE)
+        const unsigned kern = (unsigned)(ti.key >> 32);  // wave key: kernel (rebased), bc, wc
+        const unsigned bcwc = (unsigned)ti.key;
+        const unsigned kb = (unsigned)(ti.kb >> 32);     // the job's kernel base
+        const bool records = t_type == HR_STAGE_RECORDS && !t_skip;
         uint4 rec[HR_RPL];
         const unsigned base = wid * 32 * HR_RPL + lane;
 #pragma unroll
         for (int k = 0; k < HR_RPL; ++k) {
             const unsigned idx = base + k * 32;
-            rec[k] = (records && info.rb + idx < info.re) ? s_rec[(size_t)b * HR_TILE + idx]
-                                                          : make_uint4(0, 0, 0, 0xFFFFFFFFu);
+            rec[k] = (records && idx < t_n) ? s_rec[(size_t)b * HR_TILE + idx] : make_uint4(0, 0, 0, 0xFFFFFFFFu);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_empty[b]);  // the slot may be refilled now
-        if (info.region != cur) {
+        if (t_region != cur) {
             flush();
-            cur = info.region;
+            cur = t_region;
             region = regions + cur;
-            g = region->geom;
+            if (lane == 0) s_geom[wid] = region->geom;
+            __syncwarp();
             shadow = region->shadow;
             n_words = region->n_words;
         }
 
-        const unsigned s = info.stage;
-        const unsigned dep = info.dep;
-        bool ready = dep == HR_NO_DEP || dep == known || info.ready;
+        bool ready = t_dep == HR_NO_DEP || t_dep == known || t_ready;
         if (!ready) {
             unsigned r = 0;
-            if (lane == 0) r = ld_acquire_u32(&w.stages[dep].done) >= info.dep_need;
+            if (lane == 0) r = ld_acquire_u32(&w.stages[t_dep].done) >= t_need;
             ready = __shfl_sync(0xffffffffu, r, 0) != 0;
             __syncwarp();
         }
-        if (ready && dep != HR_NO_DEP) known = dep;
+        if (ready && t_dep != HR_NO_DEP) known = t_dep;
 
-        if (info.type == HR_STAGE_CLEAR && !info.skip) {
+        if (t_type == HR_STAGE_CLEAR && !t_skip) {
             if (!ready) {
                 bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error, w.wait_ns);
+                if (lane == 0) ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 __syncwarp();
                 if (!ok) break;
-                known = dep;
+                known = t_dep;
             }
             const unsigned long long span = HR_CLEAR_WORDS / HR_CONSUMERS;
-            const unsigned long long wb = (unsigned long long)info.item * HR_CLEAR_WORDS + wid * span;
+            const unsigned long long wb = (unsigned long long)t_item * HR_CLEAR_WORDS + wid * span;
             const unsigned long long we = min(n_words, wb + span);
             for (unsigned long long i = wb + 2ull * lane; i < we; i += 64ull) {
                 if (i + 1 < we)
@@ -741,12 +777,11 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                     shadow[i] = 0ull;
             }
         } else if (records) {
-            const unsigned long long wkey = info.key;
-            const unsigned bc = (unsigned)(wkey >> 16) & 0xFFFFu;
-            const unsigned wc = (unsigned)wkey & 0xFFFFu;
-            const unsigned kern = (unsigned)(wkey >> 32);
+            const unsigned bc = bcwc >> 16;
+            const unsigned wc = bcwc & 0xFFFFu;
             const unsigned ktag = kern & 7u;
             unsigned err = 0;
+            unsigned c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
             unsigned word[HR_RPL], grp[HR_RPL], tidv[HR_RPL], opv[HR_RPL];
             bool act[HR_RPL];
 #pragma unroll
@@ -754,18 +789,18 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 const uint4 v = rec[k];
                 const unsigned op = (v.w >> 16) & 0xFFu;
                 const unsigned flags = v.w >> 24;
-                const bool in = info.rb + base + k * 32 < info.re;
-                const unsigned long long key = (((unsigned long long)(v.w & 0xFFFFu) << 32) |
-                                                ((unsigned long long)(v.z >> 16) << 16) | (v.z & 0xFFFFu)) + info.kb;
+                const bool in = base + k * 32 < t_n;
+                // record key (kernel + kernel base, bc, wc) against the wave's
+                const bool same_wave = v.z == bcwc && (v.w & 0xFFFFu) + kb == kern;
                 bool a = in && op <= HR_A;
                 if (in) {
-                    if (key != wkey) err = HR_ERR_ORDER;
+                    if (!same_wave) err = HR_ERR_ORDER;
                     else if (op > HR_SYNCWARP || (op == HR_SYNCWARP && (flags & HR_RECFLAG_PARTIAL_MASK)))
                         err = HR_ERR_UNSUPPORTED;
                     else if (a && v.x >= n_words)
                         err = HR_ERR_RANGE;
                 }
-                a = a && key == wkey && v.x < n_words && wc <= HR_WC_MAX;
+                a = a && same_wave && v.x < n_words && wc <= HR_WC_MAX;
                 act[k] = a;
                 word[k] = v.x;
                 tidv[k] = v.y;
@@ -810,27 +845,24 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             if (err) hr_set_error(&region->error, err);
             __syncwarp();
 
-            if (!ready) {
-                // the previous stage is still running: touch this tile's shadow words
-                // (one 32-byte sector each, value discarded) so they sit in L2 while
-                // waiting for it, then load them fresh
-#pragma unroll
-                for (int k = 0; k < HR_RPL; ++k)
-                    if (act[k])
-                        asm volatile("{\n\t.reg .b64 t;\n\tld.relaxed.gpu.global.u64 t, [%0];\n\t}" ::"l"(shadow + word[k])
-                                     : "memory");
-                bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[dep].done, info.dep_need, &w.ctl->abort, &region->error, w.wait_ns);
-                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                __syncwarp();
-                if (!ok) break;
-                known = dep;
-            }
+            // Shadow values.  When the previous stage is still running they are
+            // loaded before waiting for it (the loads overlap the wait) and may be
+            // stale: every CAS then goes out, so a stale value fails and is refolded
+            // from the value the CAS returns.
             unsigned long long o[HR_RPL], nv[HR_RPL];
-            unsigned raced[HR_RPL], who[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k)
                 if (act[k]) o[k] = hr_ld_relaxed(shadow + word[k]);
+            const bool spec = !ready;
+            if (!ready) {
+                bool ok = true;
+                if (lane == 0) ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                __syncwarp();
+                if (!ok) break;
+                known = t_dep;
+            }
+            unsigned raced[HR_RPL], who[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
                 raced[k] = 0;
@@ -841,15 +873,17 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                         nv[k] = hr_fsm_step(o[k], tidv[k], opv[k], bc, wc, ktag, g, s_table, &raced[k]);
                     } else {
                         c_acc += __popc(grp[k]);
-                        nv[k] = fold_group(o[k], grp[k], my_acc + k * 32, bc, wc, ktag, g, s_table, &raced[k],
-                                           &who[k]);
+                        const Fold f = fold_group(o[k], grp[k], my_acc + k * 32, bc, wc, ktag, g, s_table);
+                        nv[k] = f.n;
+                        raced[k] = f.raced;
+                        who[k] = f.who;
                     }
                 }
             }
             bool need[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
-                need[k] = act[k] && nv[k] != o[k];
+                need[k] = act[k] && (spec || nv[k] != o[k]);
                 if (need[k]) nv[k] = atomicCAS(shadow + word[k], o[k], nv[k]);  // nv now holds the value seen
             }
 #pragma unroll
@@ -859,8 +893,12 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 bool done = nv[k] == o[k];
                 if (!done) {
                     c_retry++;
-                    c_cas += retry_cas(shadow + word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc, wc, ktag,
-                                       g, s_table, &raced[k], &who[k], &done, w.cas_cap);
+                    const Retry r = retry_cas(shadow + word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc,
+                                              wc, ktag, g, s_table, w.cas_cap);
+                    c_cas += r.attempts;
+                    raced[k] = r.raced;
+                    who[k] = r.who;
+                    done = r.ok != 0;
                     if (!done) hr_set_error(&region->error, HR_ERR_CONTENTION);
                 }
                 if (done && raced[k]) {
@@ -870,6 +908,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                                    kern, bc, region->region, ro, raced[k] - 1u);
                 }
             }
+            count(c_acc, c_cas, c_retry, c_merged);
         }
         // the warp's part of the tile is done; the CTA's last warp to finish it
         // publishes one completion for the stage (counters indexed by tile number
@@ -878,7 +917,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         __syncwarp();
         if (lane == 0) {
             const unsigned old = smem_add_acq_rel(&s_fin[it % (2 * HR_RING)], 1u);
-            if ((old + 1u) % HR_CONSUMERS == 0) red_release_add(&w.stages[s].done, 1u);
+            if ((old + 1u) % HR_CONSUMERS == 0) red_release_add(&w.stages[t_stage].done, 1u);
         }
     }
     flush();
