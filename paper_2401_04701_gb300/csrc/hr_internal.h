@@ -163,6 +163,9 @@ constexpr unsigned hr_variant_tile(unsigned v) { return HR_VARIANTS[v].consumers
 #ifndef HR_BATCH
 #define HR_BATCH 1
 #endif
+#ifndef HR_WAIT_SLEEP_MAX_NS
+#define HR_WAIT_SLEEP_MAX_NS 1024  // longest back-off between polls of a stage counter
+#endif
 #ifndef HR_MIN_CTAS
 #define HR_MIN_CTAS 3
 #endif

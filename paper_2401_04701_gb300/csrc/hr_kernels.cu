@@ -481,7 +481,7 @@ __device__ __forceinline__ bool stage_wait(const unsigned* done, unsigned need, 
             return false;
         }
         __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
+        if (ns < HR_WAIT_SLEEP_MAX_NS) ns <<= 1;
     }
     return true;
 }
