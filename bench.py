@@ -36,6 +36,14 @@ sys.path.insert(0, ROOT)
 METRIC = "checked accesses/sec vs HBM roofline"
 UNIT = "accesses/s"
 WORKLOAD = "global-mix: 1024x256 threads, 2^26 words, 67.1M accesses + 8.1M barrier records"
+
+
+def workload_name(n_blocks, n_words, n_acc, n_sync):
+    """Label of the global-mix workload actually run (the default is WORKLOAD)."""
+    if n_blocks == 1024:
+        return WORKLOAD
+    return "global-mix: %dx256 threads, %d words, %.1fM accesses + %.1fM barrier records" % (
+        n_blocks, n_words, n_acc / 1e6, n_sync / 1e6)
 ALG_BYTES_PER_ACCESS = 32   # 16 B record + 8 B shadow read + 8 B shadow write
 ALG_BYTES_PER_SYNC = 16     # a barrier record is streamed, not an access
 
@@ -460,9 +468,11 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_words": info["n_words"], "records": len(trace), "accesses": n_acc,
+        "config": {"workload": workload_name(args.blocks, info["n_words"], n_acc, n_sync),
+                   "n_words": info["n_words"], "records": len(trace), "accesses": n_acc,
                    "shadow_bytes_per_word": 8, "racy_words": int(len(info["injected"])),
-                   "l2": "inputs larger than L2 (1.2 GB trace, 512 MB shadow), no flush",
+                   "l2": "inputs larger than L2 (%.2f GB trace, %d MB shadow), no flush" % (
+                       len(trace) * 16 / 1e9, info["n_words"] * 8 >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
                      "frac": achieved / p_hbm, "traffic": measured_traffic() if args.blocks == 1024 else None,
@@ -522,7 +532,15 @@ def main():
         import torch
         from paper_2401_04701_gb300 import hirace
         torch.cuda.set_device(local_rank)
-        print(json.dumps({"random_access_G_ops_per_s": hirace.probe_random_access(torch.device("cuda", local_rank))}))
+        dev = torch.device("cuda", local_rank)
+        out = {"random_access_G_ops_per_s": hirace.probe_random_access(dev)}
+        # the benchmark trace's own access pattern, without ordering or state machine
+        trace, info, n_acc, n_sync = make_workload(args.blocks)
+        d_trace = torch.from_numpy(trace.view(np.uint8)).to(dev)
+        out["trace_access_ms"] = {"workload": workload_name(args.blocks, info["n_words"], n_acc, n_sync),
+                                  "accesses": n_acc, "records": len(trace),
+                                  "by_array_size": hirace.probe_trace_access(d_trace)}
+        print(json.dumps(out))
         return
     if args.serving_only:
         import torch
