@@ -46,6 +46,7 @@ def workload_name(n_blocks, n_words, n_acc, n_sync):
         n_blocks, n_words, n_acc / 1e6, n_sync / 1e6)
 ALG_BYTES_PER_ACCESS = 32   # 16 B record + 8 B shadow read + 8 B shadow write
 ALG_BYTES_PER_SYNC = 16     # a barrier record is streamed, not an access
+ALG_BYTES_PER_ACCESS_COMPACT = 24  # 16 B record + 4 B shadow read + 4 B shadow write
 
 
 KERNEL_SOURCES = ("paper_2401_04701_gb300/csrc/hr_kernels.cu", "paper_2401_04701_gb300/csrc/hr_internal.h",
@@ -250,6 +251,36 @@ def other_workloads(dev, reps=5):
         del d
         torch.cuda.empty_cache()
     return out
+
+
+def compact_shadow_workload(dev, d_trace, info, n_acc, n_sync, variant, p_hbm, reps=10):
+    """The same global-mix trace on a compact 4-byte shadow (18-bit tids, 3-bit
+    bc and wc; 256 MB instead of 512 MB).  Its algorithmic bytes are 16 B of
+    record + 4 B read + 4 B written per access."""
+    import torch
+    from paper_2401_04701_gb300 import hirace
+    reg = dict(n_words=info["n_words"], block_dim=info["block_dim"], shadow_bytes=4, tid_bits=18)
+    with hirace.Checker([reg], report_capacity=1 << 22) as ck:
+        ck.set_variant(variant)
+        ck.check_trace(0, d_trace)
+        races, status, n_total, _ = ck.report(0)
+        ok = status == hirace.HR_OK and n_total == len(info["injected"])
+        for kb in range(1, 4):
+            ck.check_trace(0, d_trace, kernel_base=kb)
+        torch.cuda.synchronize()
+        ck.profile(True)
+        ck.profile_read()
+        for kb in range(4, 4 + reps):
+            ck.check_trace(0, d_trace, kernel_base=kb)
+        torch.cuda.synchronize()
+        prof = ck.profile_read()
+        ck.profile(False)
+        _, status, _, _ = ck.report(0)
+    check_ms = prof["check_ms"] / max(1, prof["calls"])
+    alg = n_acc * ALG_BYTES_PER_ACCESS_COMPACT + n_sync * ALG_BYTES_PER_SYNC
+    return {"shadow_bytes_per_word": 4, "tid_bits": 18, "races_match": bool(ok), "status": hirace.STATUS[status],
+            "kernel_ms": check_ms, "accesses_per_s": n_acc / (check_ms / 1e3),
+            "alg_bytes_per_launch": alg, "frac_of_hbm_roofline": alg / (check_ms / 1e3) / 1e9 / p_hbm}
 
 
 def batch_workload(dev, reps=3):
@@ -489,6 +520,8 @@ def run_gpu(args, rank, world, local_rank):
     }
     if cpu:
         line["cpu_baseline"] = cpu
+    if args.blocks == 1024:
+        line["compact_shadow"] = compact_shadow_workload(dev, d_trace, info, n_acc, n_sync, best, p_hbm)
     if not args.no_instrumented:
         line["instrumented_slowdown"] = instrumented_slowdown(dev)
     if args.all_workloads:

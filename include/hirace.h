@@ -35,7 +35,7 @@ typedef enum hr_status {
     HR_ERR_CUDA = 3,           /* a CUDA runtime call failed */
     HR_ERR_ORDER = 4,          /* trace not sorted by (kernel, bc, wc), or older than the region's last record */
     HR_ERR_RANGE = 5,          /* word index >= n_words */
-    HR_ERR_CLOCK_OVERFLOW = 6, /* a clock does not fit the shadow packing (Sec. III-A footnote) */
+    HR_ERR_CLOCK_OVERFLOW = 6, /* a clock or thread id does not fit the shadow packing (Sec. III-A footnote) */
     HR_ERR_CONTENTION = 7,     /* the CAS retry cap was reached on some word */
     HR_ERR_TIMEOUT = 8,        /* a bounded device-side wait expired */
     HR_ERR_UNSUPPORTED = 9,    /* partial-mask __syncwarp or an unknown op code */
@@ -109,7 +109,10 @@ typedef struct hr_region_desc {
     uint32_t block_dim;       /* threads per block of the traced kernels, >= 1 */
     uint32_t warp_size;       /* 32 on NVIDIA GPUs; 1..32 for small test universes */
     uint32_t space;           /* HR_SPACE_GLOBAL or HR_SPACE_SHARED (informational) */
-    uint32_t reserved;        /* must be 0 */
+    uint8_t shadow_bytes;     /* bytes per shadow word: 8 (0 = default) or 4 (compact packing) */
+    uint8_t tid_bits;         /* compact packing only: tid field width, 4..22 (0 = 16); bc and wc
+                                 share the other 24 - tid_bits bits (hirace_device.cuh) */
+    uint16_t reserved;        /* must be 0 */
     uint64_t report_capacity; /* race records kept for this region; 0 = the hr_init default */
 } hr_region_desc;
 
@@ -121,9 +124,10 @@ typedef struct hr_region_desc {
  *   regions          n_regions host descriptors
  *   report_capacity  default race records per region (>= 1)
  *   stream           stream for the initial clears
- * The context owns all device memory it allocates (shadow: 8*n_words bytes
- * per region; report ring: 16*report_capacity bytes per region; a wave table
- * and control block).  Errors: HR_ERR_INVALID, HR_ERR_OOM, HR_ERR_CUDA.
+ * The context owns all device memory it allocates (shadow: shadow_bytes *
+ * n_words bytes per region; report ring: 16*report_capacity bytes per region;
+ * a wave table and control block).  Errors: HR_ERR_INVALID (also for a
+ * compact region whose block_dim exceeds 2^tid_bits), HR_ERR_OOM, HR_ERR_CUDA.
  */
 hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
                   uint64_t report_capacity, hr_stream_t stream);

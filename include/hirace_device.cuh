@@ -24,6 +24,16 @@
  * and needs no atomic at all:
  *     thread scope: tid, bc, wc      warp scope: warp's first tid, bc, wc
  *     block scope:  block's first tid, bc      grid scope and RACE: nothing
+ *
+ * Compact shadow value, 4 bytes per word (the shadow size is configurable,
+ * Sec. IV-B), for regions whose thread ids fit T = tid_bits bits:
+ *     bits 31..27  FSM state        bits 26..24  kernel tag
+ *     bits 23..T+W bc (B = 24 - T - W bits)
+ *     bits T+W-1..T wc (W = (24 - T) / 2 bits)     bits T-1..0  tid
+ * e.g. T = 16: bc and wc 4 bits each; T = 18: 3 bits each.  The state
+ * machine runs on the 8-byte layout; the compact word is only its storage
+ * form (hr_expand32 / hr_compress64), so both sizes take the same
+ * transitions.  A tid, bc or wc beyond its width is HR_ERR_CLOCK_OVERFLOW.
  */
 #ifndef HIRACE_DEVICE_CUH
 #define HIRACE_DEVICE_CUH
@@ -68,8 +78,10 @@ typedef struct hr_geom {
     uint32_t warp_size;
     uint64_t bd_magic;
     uint64_t ws_magic;
-    uint32_t bd_shift; /* log2(block_dim) when block_dim and warp_size are both powers of two, else ~0u */
-    uint32_t ws_shift; /* log2(warp_size) in that case */
+    uint32_t bd_shift;     /* log2(block_dim) when block_dim and warp_size are both powers of two, else ~0u */
+    uint32_t ws_shift;     /* log2(warp_size) in that case */
+    uint32_t shadow_bytes; /* 8, or 4 for the compact packing */
+    uint32_t tid_bits;     /* compact packing: width of the tid field (4..22) */
 } hr_geom;
 
 /* Everything an instrumented kernel needs for one region; pass by value. */
@@ -174,6 +186,61 @@ static __device__ __forceinline__ uint64_t hr_ld_relaxed(const unsigned long lon
     return v;
 }
 
+static __device__ __forceinline__ uint32_t hr_ld_relaxed32(const unsigned int* p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+/* widths of the compact packing's clock fields */
+static __device__ __forceinline__ uint32_t hr_wc_bits(const hr_geom& g) { return (24u - g.tid_bits) >> 1; }
+static __device__ __forceinline__ uint32_t hr_bc_bits(const hr_geom& g) { return 24u - g.tid_bits - hr_wc_bits(g); }
+
+/* Whether an access's identity and clocks fit the region's packing. */
+static __device__ __forceinline__ bool hr_fits(uint32_t tid, uint32_t bc, uint32_t wc, const hr_geom& g)
+{
+    if (g.shadow_bytes != 4) return bc <= HR_BC_MAX && wc <= HR_WC_MAX;
+    return (tid >> g.tid_bits) == 0 && (wc >> hr_wc_bits(g)) == 0 && (bc >> hr_bc_bits(g)) == 0;
+}
+
+/* compact storage form -> the 8-byte layout */
+static __device__ __forceinline__ uint64_t hr_expand32(uint32_t x, const hr_geom& g)
+{
+    const uint32_t t = g.tid_bits, w = hr_wc_bits(g);
+    const uint32_t tid = x & ((1u << t) - 1u);
+    const uint32_t wc = (x >> t) & ((1u << w) - 1u);
+    const uint32_t bc = (x & 0x00FFFFFFu) >> (t + w);
+    return ((uint64_t)(x >> 24) << HR_SH_KTAG_SHIFT) | ((uint64_t)bc << HR_SH_BC_SHIFT) |
+           ((uint64_t)wc << HR_SH_WC_SHIFT) | tid;
+}
+
+/* 8-byte layout -> compact storage form (fields must fit, see hr_fits) */
+static __device__ __forceinline__ uint32_t hr_compress64(uint64_t v, const hr_geom& g)
+{
+    const uint32_t t = g.tid_bits, w = hr_wc_bits(g);
+    const uint32_t wc = (uint32_t)(v >> HR_SH_WC_SHIFT) & 0xFFu;
+    const uint32_t bc = (uint32_t)(v >> HR_SH_BC_SHIFT) & 0xFFFFu;
+    return ((uint32_t)(v >> HR_SH_KTAG_SHIFT) << 24) | (bc << (t + w)) | (wc << t) | (uint32_t)v;
+}
+
+/* Shadow word `word` of a region, in the 8-byte layout whatever its storage size. */
+static __device__ __forceinline__ uint64_t hr_shadow_load(unsigned long long* shadow, unsigned long long word,
+                                                          const hr_geom& g)
+{
+    if (g.shadow_bytes == 4) return hr_expand32(hr_ld_relaxed32((unsigned int*)shadow + word), g);
+    return hr_ld_relaxed(shadow + word);
+}
+
+/* CAS of shadow word `word` from o to n (8-byte layout); returns the value seen. */
+static __device__ __forceinline__ uint64_t hr_shadow_cas(unsigned long long* shadow, unsigned long long word,
+                                                         uint64_t o, uint64_t n, const hr_geom& g)
+{
+    if (g.shadow_bytes == 4)
+        return hr_expand32(atomicCAS((unsigned int*)shadow + word, hr_compress64(o, g), hr_compress64(n, g)), g);
+    return atomicCAS(shadow + word, (unsigned long long)o, (unsigned long long)n);
+}
+
 static __device__ __forceinline__ void hr_set_error(unsigned int* err, unsigned int code)
 {
     atomicCAS(err, 0u, code);
@@ -245,18 +312,17 @@ static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long
         hr_set_error(v.error, word >= v.n_words ? HR_ERR_RANGE : HR_ERR_UNSUPPORTED);
         return;
     }
-    if (c.bc > HR_BC_MAX || c.wc > HR_WC_MAX) {
+    if (!hr_fits(c.tid, c.bc, c.wc, v.geom)) {
         hr_set_error(v.error, HR_ERR_CLOCK_OVERFLOW);
         return;
     }
-    unsigned long long* p = v.shadow + word;
     const uint32_t ktag = v.kernel & 7u;
-    uint64_t o = hr_ld_relaxed(p);
+    uint64_t o = hr_shadow_load(v.shadow, word, v.geom);
     for (int it = 0; it < HR_CAS_RETRY_CAP; ++it) {
         uint32_t raced = 0;
         const uint64_t n = hr_fsm_step(o, c.tid, op, c.bc, c.wc, ktag, v.geom, v.table, &raced);
         if (n == o) return;
-        const uint64_t prev = atomicCAS(p, (unsigned long long)o, (unsigned long long)n);
+        const uint64_t prev = hr_shadow_cas(v.shadow, word, o, n, v.geom);
         if (prev == o) {
             if (raced)
                 hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)word, c.tid, v.kernel, c.bc,

@@ -130,6 +130,13 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         if (d.n_words == 0 || d.n_words > (1ull << 32) || d.block_dim == 0 || d.warp_size == 0 ||
             d.warp_size > 32 || d.reserved != 0 || d.space > HR_SPACE_SHARED)
             return HR_ERR_INVALID;
+        if (d.shadow_bytes != 0 && d.shadow_bytes != 4 && d.shadow_bytes != 8) return HR_ERR_INVALID;
+        if (d.shadow_bytes == 4) {
+            const uint32_t t = hr_desc_tid_bits(d);
+            if (t < 4 || t > 22 || d.block_dim > (1u << t)) return HR_ERR_INVALID;
+        } else if (d.tid_bits != 0) {
+            return HR_ERR_INVALID;
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
     hr_ctx* c = new (std::nothrow) hr_ctx;
@@ -151,7 +158,7 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         r.ring_cap = regions[i].report_capacity ? regions[i].report_capacity : report_capacity;
         r.d = c->d_regions + i;
         r.capacity = r.desc.n_words;
-        e = cudaMalloc(&r.shadow, r.desc.n_words * sizeof(unsigned long long));
+        e = cudaMalloc(&r.shadow, r.desc.n_words * hr_desc_shadow_bytes(r.desc));
         if (e == cudaSuccess) e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
         // scratch of one trace check: job table, interval counts, wave table, stages, control block
         const size_t total = hr_work_bytes(1, HR_MAX_INTERVALS, max_waves);
@@ -160,7 +167,7 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
             r.work = hr_work_at(r.work_mem, 1, HR_MAX_INTERVALS, max_waves);
             e = cudaMemsetAsync(r.work_mem, 0, total, s);
         }
-        if (e == cudaSuccess) e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * hr_desc_shadow_bytes(r.desc), s);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming);
         hr_region_dev& h = hdev[i];
         memset(&h, 0, sizeof h);
@@ -169,7 +176,7 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         h.n_words = r.desc.n_words;
         h.ring_cap = r.ring_cap;
         h.region = i;
-        h.geom = hr_make_geom(r.desc.block_dim, r.desc.warp_size);
+        h.geom = hr_desc_geom(r.desc);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_regions, hdev.data(), sizeof(hr_region_dev) * n_regions, cudaMemcpyHostToDevice, s);
@@ -326,7 +333,7 @@ extern "C" hr_status hr_sync(hr_ctx* ctx, uint32_t region, uint32_t scope, hr_st
     // when the next kernel starts a new group of 8, clear the shadow
     cudaError_t e = cudaSuccess;
     if (((r.kernel + 1) >> 3) != (r.kernel >> 3))
-        e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * sizeof(unsigned long long), s);
+        e = cudaMemsetAsync(r.shadow, 0, r.desc.n_words * hr_desc_shadow_bytes(r.desc), s);
     if (e == cudaSuccess) e = hr_launch_sync_kernel(r.d, s);
     if (e == cudaSuccess) e = mark_done(r, s);
     if (e == cudaSuccess) r.kernel++;
@@ -378,7 +385,7 @@ extern "C" hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream)
     RegionHost& r = ctx->regions[region];
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();  // report only errors of this call's launches
-    cudaError_t e = hr_launch_reset(r.d, r.shadow, r.desc.n_words, s);
+    cudaError_t e = hr_launch_reset(r.d, r.shadow, r.desc.n_words * hr_desc_shadow_bytes(r.desc), s);
     if (e == cudaSuccess) e = mark_done(r, s);
     r.kernel = 0;
     return cuda_status(e);
@@ -391,13 +398,14 @@ extern "C" hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_
     RegionHost& r = ctx->regions[region];
     if (n_words == 0 || n_words > r.capacity || block_dim == 0 || warp_size == 0 || warp_size > 32)
         return HR_ERR_INVALID;
+    if (r.desc.shadow_bytes == 4 && block_dim > (1u << hr_desc_tid_bits(r.desc))) return HR_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();  // report only errors of this call's launches
     r.desc.n_words = n_words;
     r.desc.block_dim = block_dim;
     r.desc.warp_size = warp_size;
-    cudaError_t e = hr_launch_reconfigure(r.d, n_words, hr_make_geom(block_dim, warp_size), s);
-    if (e == cudaSuccess) e = hr_launch_reset(r.d, r.shadow, n_words, s);
+    cudaError_t e = hr_launch_reconfigure(r.d, n_words, hr_desc_geom(r.desc), s);
+    if (e == cudaSuccess) e = hr_launch_reset(r.d, r.shadow, n_words * hr_desc_shadow_bytes(r.desc), s);
     if (e == cudaSuccess) e = mark_done(r, s);
     r.kernel = 0;
     return cuda_status(e);
@@ -424,7 +432,7 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     out->table = ctx->d_table;
     out->n_words = r.desc.n_words;
     out->ring_cap = r.ring_cap;
-    out->geom = hr_make_geom(r.desc.block_dim, r.desc.warp_size);
+    out->geom = hr_desc_geom(r.desc);
     out->kernel = r.kernel;
     out->region = region;
     return HR_OK;

@@ -6,8 +6,9 @@
 #include "../../include/hirace.h"
 #include "../../include/hirace_device.cuh"
 
-// Geometry with exact reciprocals and, when both sizes are powers of two, shifts.
-inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size)
+// Geometry with exact reciprocals and, when both sizes are powers of two,
+// shifts; plus the shadow packing (8 bytes, or 4 with a tid_bits-wide tid).
+inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size, uint32_t shadow_bytes = 8, uint32_t tid_bits = 0)
 {
     auto magic = [](uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; };
     auto log2_exact = [](uint32_t d) -> uint32_t {
@@ -24,7 +25,20 @@ inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size)
     const uint32_t bs = log2_exact(block_dim), ws = log2_exact(warp_size);
     g.bd_shift = (bs != ~0u && ws != ~0u) ? bs : ~0u;
     g.ws_shift = (bs != ~0u && ws != ~0u) ? ws : ~0u;
+    g.shadow_bytes = shadow_bytes == 4 ? 4u : 8u;
+    g.tid_bits = g.shadow_bytes == 4 ? (tid_bits ? tid_bits : 16u) : 0u;
     return g;
+}
+
+// Bytes per shadow word and tid width of a region descriptor (defaults applied).
+inline uint32_t hr_desc_shadow_bytes(const hr_region_desc& d) { return d.shadow_bytes == 4 ? 4u : 8u; }
+inline uint32_t hr_desc_tid_bits(const hr_region_desc& d)
+{
+    return d.shadow_bytes == 4 ? (d.tid_bits ? d.tid_bits : 16u) : 0u;
+}
+inline hr_geom hr_desc_geom(const hr_region_desc& d)
+{
+    return hr_make_geom(d.block_dim, d.warp_size, hr_desc_shadow_bytes(d), hr_desc_tid_bits(d));
 }
 
 // Per-region state in device memory.
@@ -187,7 +201,7 @@ void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsig
 int hr_check_grid_size(unsigned variant);
 constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
-cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long n_words,
+cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long shadow_bytes,
                             cudaStream_t stream);
 cudaError_t hr_launch_reconfigure(hr_region_dev* d_region, unsigned long long n_words, hr_geom geom,
                                   cudaStream_t stream);

@@ -528,9 +528,10 @@ struct Retry {
 // Cold path: the first CAS lost a race (or validated a stale speculative
 // load).  Re-fold from the value it returned until a CAS sticks or the retry
 // cap is reached.
-__device__ __noinline__ Retry retry_cas(unsigned long long* p, unsigned long long seen, unsigned tid, unsigned op,
-                                        unsigned grp, const Acc* acc, unsigned bc, unsigned wc, unsigned ktag,
-                                        const hr_geom& g, const unsigned char* table, unsigned cap)
+__device__ __noinline__ Retry retry_cas(unsigned long long* shadow, unsigned word, unsigned long long seen,
+                                        unsigned tid, unsigned op, unsigned grp, const Acc* acc, unsigned bc,
+                                        unsigned wc, unsigned ktag, const hr_geom& g, const unsigned char* table,
+                                        unsigned cap)
 {
     const unsigned lane = threadIdx.x & 31;
     Retry r{0u, lane, 0u, 0u};
@@ -548,7 +549,7 @@ __device__ __noinline__ Retry retry_cas(unsigned long long* p, unsigned long lon
             return r;
         }
         r.attempts++;
-        seen = atomicCAS(p, o, f.n);
+        seen = hr_shadow_cas(shadow, word, o, f.n, g);
         if (seen == o) {
             r.ok = 1;
             return r;
@@ -767,14 +768,17 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 if (!ok) break;
                 known = t_dep;
             }
-            const unsigned long long span = HR_CLEAR_WORDS / HR_CONSUMERS;
-            const unsigned long long wb = (unsigned long long)t_item * HR_CLEAR_WORDS + wid * span;
-            const unsigned long long we = min(n_words, wb + span);
-            for (unsigned long long i = wb + 2ull * lane; i < we; i += 64ull) {
-                if (i + 1 < we)
-                    *reinterpret_cast<ulonglong2*>(shadow + i) = make_ulonglong2(0ull, 0ull);
+            // bytes [bb, be) of the shadow: 16-byte stores, a 4-byte tail
+            const unsigned long long sb = g.shadow_bytes;
+            const unsigned long long span = (unsigned long long)(HR_CLEAR_WORDS / HR_CONSUMERS) * sb;
+            const unsigned long long bb = (unsigned long long)t_item * HR_CLEAR_WORDS * sb + wid * span;
+            const unsigned long long be = min(n_words * sb, bb + span);
+            unsigned char* base8 = reinterpret_cast<unsigned char*>(shadow);
+            for (unsigned long long i = bb + 16ull * lane; i < be; i += 512ull) {
+                if (i + 16 <= be)
+                    *reinterpret_cast<ulonglong2*>(base8 + i) = make_ulonglong2(0ull, 0ull);
                 else
-                    shadow[i] = 0ull;
+                    for (unsigned long long j = i; j < be; j += 4) *reinterpret_cast<unsigned*>(base8 + j) = 0u;
             }
         } else if (records) {
             const unsigned bc = bcwc >> 16;
@@ -800,7 +804,11 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                     else if (a && v.x >= n_words)
                         err = HR_ERR_RANGE;
                 }
-                a = a && same_wave && v.x < n_words && wc <= HR_WC_MAX;
+                if (a && same_wave && v.x < n_words && !hr_fits(v.y, bc, wc, g)) {
+                    err = HR_ERR_CLOCK_OVERFLOW;  // tid, bc or wc wider than the shadow packing
+                    a = false;
+                }
+                a = a && same_wave && v.x < n_words;
                 act[k] = a;
                 word[k] = v.x;
                 tidv[k] = v.y;
@@ -841,7 +849,6 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                     }
                 }
             }
-            if (wc > HR_WC_MAX) err = HR_ERR_CLOCK_OVERFLOW;
             if (err) hr_set_error(&region->error, err);
             __syncwarp();
 
@@ -852,7 +859,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             unsigned long long o[HR_RPL], nv[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k)
-                if (act[k]) o[k] = hr_ld_relaxed(shadow + word[k]);
+                if (act[k]) o[k] = hr_shadow_load(shadow, word[k], g);
             const bool spec = !ready;
             if (!ready) {
                 bool ok = true;
@@ -884,7 +891,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
                 need[k] = act[k] && (spec || nv[k] != o[k]);
-                if (need[k]) nv[k] = atomicCAS(shadow + word[k], o[k], nv[k]);  // nv now holds the value seen
+                if (need[k]) nv[k] = hr_shadow_cas(shadow, word[k], o[k], nv[k], g);  // nv now holds the value seen
             }
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
@@ -893,7 +900,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 bool done = nv[k] == o[k];
                 if (!done) {
                     c_retry++;
-                    const Retry r = retry_cas(shadow + word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc,
+                    const Retry r = retry_cas(shadow, word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc,
                                               wc, ktag, g, s_table, w.cas_cap);
                     c_cas += r.attempts;
                     raced[k] = r.raced;
@@ -1056,10 +1063,10 @@ cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long n_words,
+cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long shadow_bytes,
                             cudaStream_t stream)
 {
-    cudaError_t e = cudaMemsetAsync(shadow, 0, n_words * sizeof(unsigned long long), stream);
+    cudaError_t e = cudaMemsetAsync(shadow, 0, shadow_bytes, stream);
     if (e != cudaSuccess) return e;
     hr_reset_state<<<1, 1, 0, stream>>>(d_region);
     return cudaGetLastError();

@@ -30,12 +30,14 @@ SYNC_KERNEL = 0
 
 class HrRegionDesc(ctypes.Structure):
     _fields_ = [("n_words", ctypes.c_uint64), ("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32),
-                ("space", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("report_capacity", ctypes.c_uint64)]
+                ("space", ctypes.c_uint32), ("shadow_bytes", ctypes.c_uint8), ("tid_bits", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint16), ("report_capacity", ctypes.c_uint64)]
 
 
 class HrGeom(ctypes.Structure):
     _fields_ = [("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32), ("bd_magic", ctypes.c_uint64),
-                ("ws_magic", ctypes.c_uint64), ("bd_shift", ctypes.c_uint32), ("ws_shift", ctypes.c_uint32)]
+                ("ws_magic", ctypes.c_uint64), ("bd_shift", ctypes.c_uint32), ("ws_shift", ctypes.c_uint32),
+                ("shadow_bytes", ctypes.c_uint32), ("tid_bits", ctypes.c_uint32)]
 
 
 class HrJob(ctypes.Structure):
@@ -51,7 +53,7 @@ class HrView(ctypes.Structure):
                 ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32)]
 
 
-assert ctypes.sizeof(HrView) == 104
+assert ctypes.sizeof(HrView) == 112
 
 
 class HiRaceError(RuntimeError):
@@ -168,7 +170,9 @@ class Checker:
     """One checker context with one shadow store per region.
 
     ``regions`` is a list of dicts with keys n_words, block_dim and optional
-    warp_size (32), space (global), report_capacity (0 = the default).
+    warp_size (32), space (global), report_capacity (0 = the default),
+    shadow_bytes (8, or 4 for the compact packing) and tid_bits (compact
+    packing: tid width, 0 = 16).
     """
 
     def __init__(self, regions, report_capacity: int = 1 << 20, stream=None):
@@ -179,6 +183,8 @@ class Checker:
             arr[i].block_dim = int(r["block_dim"])
             arr[i].warp_size = int(r.get("warp_size", 32))
             arr[i].space = int(r.get("space", SPACE_GLOBAL))
+            arr[i].shadow_bytes = int(r.get("shadow_bytes", 0))
+            arr[i].tid_bits = int(r.get("tid_bits", 0))
             arr[i].reserved = 0
             arr[i].report_capacity = int(r.get("report_capacity", 0))
         self.regions = [dict(r) for r in regions]

@@ -52,3 +52,23 @@ def test_host_only_calls(lib):
     assert lib.hr_init(ctypes.byref(out), None, 1, 1, None) == 1
     lib.hr_destroy.argtypes = [ctypes.c_void_p]
     assert lib.hr_destroy(None) == 1
+
+
+@pytest.mark.parametrize("bad", [dict(shadow_bytes=3), dict(shadow_bytes=8, tid_bits=16),
+                                 dict(shadow_bytes=4, tid_bits=3), dict(shadow_bytes=4, tid_bits=23),
+                                 dict(shadow_bytes=4, tid_bits=8, block_dim=512), dict(reserved=1)])
+def test_init_rejects_bad_shadow_packing(lib, bad):
+    """A compact region needs 4 <= tid_bits <= 22 and block_dim <= 2^tid_bits; an
+    8-byte region takes no tid width (checked before any CUDA call)."""
+    from paper_2401_04701_gb300 import hirace
+    arr = (hirace.HrRegionDesc * 1)()
+    arr[0].n_words = 64
+    arr[0].block_dim = bad.get("block_dim", 256)
+    arr[0].warp_size = 32
+    arr[0].shadow_bytes = bad.get("shadow_bytes", 0)
+    arr[0].tid_bits = bad.get("tid_bits", 0)
+    arr[0].reserved = bad.get("reserved", 0)
+    lib.hr_init.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p]
+    out = ctypes.c_void_p()
+    assert lib.hr_init(ctypes.byref(out), arr, 1, 1024, None) == 1
+    assert not out.value
