@@ -149,13 +149,21 @@ def make_workload(n_blocks=1024):
     return trace, info, n_acc, n_sync
 
 
-def cpu_oracle_rate(trace, info, n_acc, max_records=None):
-    """Serial FSM oracle (C, one core) over a sample of the trace: (accesses/s, seconds, sample)."""
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def cpu_oracle_rate(trace, info, n_acc, max_records=None, threads=1):
+    """Serial FSM oracle (C) over a sample of the trace, on one core or on
+    `threads` cores (disjoint word ranges): (accesses/s, seconds, accesses)."""
     from oracle import oracle
     sample = trace if max_records is None else trace[:max_records]
     acc = int(np.count_nonzero(sample["op"] <= 2)) if max_records is not None else n_acc
     t0 = time.perf_counter()
-    oracle.serial_fsm(sample, info["block_dim"], info["n_words"])
+    if threads > 1:
+        oracle.serial_fsm_parallel(sample, info["block_dim"], info["n_words"], threads=threads)
+    else:
+        oracle.serial_fsm(sample, info["block_dim"], info["n_words"])
     dt = time.perf_counter() - t0
     return acc / dt, dt, acc
 
@@ -386,20 +394,22 @@ def run_reference(args, rank, world):
     trace, info, n_acc, n_sync = make_workload()
     # bounded sample: the first block epoch (bc == 0) of the same trace
     cut = int(np.searchsorted((trace["bc"] > 0).view(np.uint8), 1))
+    cores = host_cores()
     for _ in range(args.warmup):
-        cpu_oracle_rate(trace, info, n_acc, max_records=cut)
+        cpu_oracle_rate(trace, info, n_acc, max_records=cut, threads=cores)
     tot_acc, tot_t = 0, 0.0
     for _ in range(args.steps):
-        _, dt, acc = cpu_oracle_rate(trace, info, n_acc, max_records=cut)
+        _, dt, acc = cpu_oracle_rate(trace, info, n_acc, max_records=cut, threads=cores)
         tot_acc += acc
         tot_t += dt
     value = tot_acc / tot_t
-    sample = "first block epoch of the workload (%d records, %d accesses), serial FSM oracle" % (cut, tot_acc // args.steps)
+    sample = ("first block epoch of the workload (%d records, %d accesses), serial FSM oracle on %d word "
+              "ranges, one host thread each" % (cut, tot_acc // args.steps, cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bc==0 epoch"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -492,9 +502,13 @@ def run_gpu(args, rank, world, local_rank):
     achieved = alg_bytes / (check_ms / 1e3) / 1e9
     cpu = None
     if not args.no_cpu_baseline and args.blocks == 1024:
-        rate, dt, acc = cpu_oracle_rate(trace, info, n_acc)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "whole workload once (%d accesses, %.1f s), serial FSM oracle in C" % (acc, dt)}
+        cores = host_cores()
+        rate, dt, acc = cpu_oracle_rate(trace, info, n_acc, threads=cores)
+        rate1, dt1, _ = cpu_oracle_rate(trace, info, n_acc)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "whole workload once (%d accesses, %.1f s): serial FSM oracle in C on %d disjoint "
+                         "word ranges, one host thread each" % (acc, dt, cores),
+                "single_core": {"value": rate1, "cores": 1, "seconds": dt1}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

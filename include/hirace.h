@@ -133,6 +133,22 @@ hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_region
                   uint64_t report_capacity, hr_stream_t stream);
 
 /*
+ * hr_init_with_buffers - hr_init over shadow stores (and optionally report
+ * rings) the caller already owns, e.g. tensors from a framework's allocator.
+ *   shadows  n_regions device pointers, each to shadow_bytes * n_words bytes,
+ *            16-byte aligned; every word is set to INIT (zero) on `stream`
+ *   rings    NULL, or n_regions device pointers (NULL entries: allocated by
+ *            the context) to 16 * capacity bytes, 16-byte aligned
+ * The caller keeps ownership: the buffers must outlive the context and are
+ * not freed by hr_destroy; nothing else may write them while it lives.  The
+ * context still allocates its own scratch.  Errors: those of hr_init, and
+ * HR_ERR_INVALID for a NULL or misaligned buffer.
+ */
+hr_status hr_init_with_buffers(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
+                               uint64_t report_capacity, void* const* shadows, hr_race* const* rings,
+                               hr_stream_t stream);
+
+/*
  * hr_check_trace - apply a device-resident trace to one region (Algorithm 1
  * for every access record, in an order consistent with happens-before).
  *   d_trace  n records in device memory, caller-owned, alive until `stream`

@@ -505,3 +505,38 @@ int64_t hro_serial_fsm(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_
     free(sh);
     return nr;
 }
+
+/* The serial FSM restricted to the words in [lo, hi): the same per-word
+ * processing in trace order, so the union of the reports of disjoint ranges
+ * is the report set of hro_serial_fsm (used to run the oracle on several
+ * host cores, one range per thread).  Returns the report count or -1/-2. */
+uint64_t hro_word_bytes(void) { return sizeof(hro_word); }
+
+/* `sh` is the caller's zeroed array of hi - lo word summaries (so that one
+ * allocation, faulted in once, serves every range). */
+int64_t hro_serial_fsm_range(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_t warp_size,
+                             uint64_t lo, uint64_t hi, uint64_t n_words, hro_word* sh, hro_report* out,
+                             uint64_t cap)
+{
+    if (hi > n_words) hi = n_words;
+    if (lo > hi) lo = hi;
+    if (!sh) return -2;
+    int64_t nr = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        const hro_rec* x = &r[i];
+        if (!is_access(x->op)) continue;
+        if (x->word >= n_words) return -1;
+        if (x->word < lo || x->word >= hi) continue;
+        if (fsm_apply(&sh[x->word - lo], x, block_dim, warp_size)) {
+            if ((uint64_t)nr < cap) {
+                out[nr].word = x->word;
+                out[nr].tid = x->tid;
+                out[nr].kernel = x->kernel;
+                out[nr].epoch = x->bc;
+                out[nr].op = x->op;
+            }
+            nr++;
+        }
+    }
+    return nr;
+}

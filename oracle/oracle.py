@@ -9,7 +9,9 @@ trace record layout on its own.
 * ``bruteforce``   - the race definition (Sec. II-A, II-B), every pair of
                      accesses per (kernel, word); C code in ``hr_oracle.c``.
 * ``serial_fsm``   - a serial restatement of the parallel FSM (Sec. III,
-                     Algorithm 1) in C, one record at a time.
+                     Algorithm 1) in C, one record at a time;
+                     ``serial_fsm_parallel`` runs it on disjoint word ranges,
+                     one host thread each (the CPU baseline on all cores).
 * ``hb_races``     - a second, pure-Python statement of the definition for
                      tiny traces: happens-before is *reachability* over
                      program order and barrier edges (the textbook relation
@@ -71,6 +73,10 @@ def _lib():
         lib.hro_group_check.restype = ctypes.c_int
         lib.hro_serial_fsm.argtypes = [P, u64, u32, u32, u64, P, u64, P]
         lib.hro_serial_fsm.restype = i64
+        lib.hro_serial_fsm_range.argtypes = [P, u64, u32, u32, u64, u64, u64, P, P, u64]
+        lib.hro_serial_fsm_range.restype = i64
+        lib.hro_word_bytes.argtypes = []
+        lib.hro_word_bytes.restype = u64
         _lib_handle = lib
     return _lib_handle
 
@@ -137,6 +143,44 @@ def serial_fsm(trace, block_dim: int, n_words: int, warp_size: int = 32, names: 
         if n <= cap:
             return (out[:n], nm) if names else out[:n]
         cap = int(n)
+
+
+def serial_fsm_parallel(trace, block_dim: int, n_words: int, warp_size: int = 32, threads: int = 0):
+    """serial_fsm over `threads` disjoint word ranges at once (one host thread
+    each; the C calls release the GIL).  Same report set as serial_fsm, in
+    range order.  threads=0: every core this process may run on."""
+    from concurrent.futures import ThreadPoolExecutor
+    rec = _as_records(trace)
+    if threads <= 0:
+        threads = len(os.sched_getaffinity(0))
+    threads = max(1, min(threads, n_words))
+    bounds = [n_words * i // threads for i in range(threads + 1)]
+    # one zeroed array of word summaries, written once here so the threads do
+    # not take its page faults one at a time
+    wb = int(_lib().hro_word_bytes())
+    summaries = np.empty(n_words * wb, np.uint8)
+    summaries.fill(0)
+
+    def run(i):
+        cap = 1 << 12
+        sh = summaries[bounds[i] * wb:]
+        while True:
+            out = np.zeros(cap, REPORT_DT)
+            sh[:(bounds[i + 1] - bounds[i]) * wb].fill(0)
+            n = _lib().hro_serial_fsm_range(_ptr(rec), len(rec), block_dim, warp_size, bounds[i], bounds[i + 1],
+                                            n_words, _ptr(sh), _ptr(out), cap)
+            if n == -1:
+                raise ValueError("word index out of range")
+            if n < 0:
+                raise MemoryError("oracle could not allocate the word summaries")
+            if n <= cap:
+                return out[:n]
+            cap = int(n)
+
+    _lib()
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(run, range(threads)))
+    return np.concatenate(parts) if parts else np.zeros(0, REPORT_DT)
 
 
 def race_keys(arr) -> set:

@@ -20,6 +20,8 @@ struct RegionHost {
     void* work_mem = nullptr;
     hr_work work{};
     unsigned kernel = 0;                  // kernel ordinal seen by device views
+    bool owns_shadow = true;              // false: caller-owned (hr_init_with_buffers)
+    bool owns_ring = true;
     cudaEvent_t done = nullptr;           // recorded after every call on the region
     bool captured = false;                // work was queued inside a stream capture
 };
@@ -99,8 +101,8 @@ static void free_ctx(hr_ctx* c)
     if (!c) return;
     for (auto& r : c->regions) {
         if (r.done) cudaEventDestroy(r.done);
-        cudaFree(r.shadow);
-        cudaFree(r.ring);
+        if (r.owns_shadow) cudaFree(r.shadow);
+        if (r.owns_ring) cudaFree(r.ring);
         cudaFree(r.work_mem);
     }
     for (auto* v : {&c->calls, &c->spare})
@@ -119,8 +121,8 @@ static void free_ctx(hr_ctx* c)
 static bool valid_region(hr_ctx* ctx, uint32_t region) { return ctx && region < ctx->regions.size(); }
 static hr_status fetch_region(hr_ctx* ctx, uint32_t region, hr_region_dev* out);
 
-extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
-                             uint64_t report_capacity, hr_stream_t stream)
+static hr_status init_impl(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions, uint64_t report_capacity,
+                           void* const* shadows, hr_race* const* rings, hr_stream_t stream)
 {
     if (!out) return HR_ERR_INVALID;
     *out = nullptr;
@@ -158,8 +160,18 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
         r.ring_cap = regions[i].report_capacity ? regions[i].report_capacity : report_capacity;
         r.d = c->d_regions + i;
         r.capacity = r.desc.n_words;
-        e = cudaMalloc(&r.shadow, r.desc.n_words * hr_desc_shadow_bytes(r.desc));
-        if (e == cudaSuccess) e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
+        r.owns_shadow = !(shadows && shadows[i]);
+        r.owns_ring = !(rings && rings[i]);
+        if (r.owns_shadow)
+            e = cudaMalloc(&r.shadow, r.desc.n_words * hr_desc_shadow_bytes(r.desc));
+        else
+            r.shadow = (unsigned long long*)shadows[i];
+        if (e == cudaSuccess) {
+            if (r.owns_ring)
+                e = cudaMalloc(&r.ring, r.ring_cap * sizeof(hr_race));
+            else
+                r.ring = rings[i];
+        }
         // scratch of one trace check: job table, interval counts, wave table, stages, control block
         const size_t total = hr_work_bytes(1, HR_MAX_INTERVALS, max_waves);
         if (e == cudaSuccess) e = cudaMalloc(&r.work_mem, total);
@@ -188,6 +200,24 @@ extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32
     }
     *out = c;
     return HR_OK;
+}
+
+extern "C" hr_status hr_init(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
+                             uint64_t report_capacity, hr_stream_t stream)
+{
+    return init_impl(out, regions, n_regions, report_capacity, nullptr, nullptr, stream);
+}
+
+extern "C" hr_status hr_init_with_buffers(hr_ctx** out, const hr_region_desc* regions, uint32_t n_regions,
+                                          uint64_t report_capacity, void* const* shadows, hr_race* const* rings,
+                                          hr_stream_t stream)
+{
+    if (!shadows) return HR_ERR_INVALID;
+    for (uint32_t i = 0; i < n_regions && regions; ++i) {
+        if (!shadows[i] || ((uintptr_t)shadows[i] & 15u)) return HR_ERR_INVALID;  // 16-byte clears
+        if (rings && rings[i] && ((uintptr_t)rings[i] & 15u)) return HR_ERR_INVALID;
+    }
+    return init_impl(out, regions, n_regions, report_capacity, shadows, rings, stream);
 }
 
 static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,

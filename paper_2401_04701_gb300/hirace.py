@@ -77,6 +77,8 @@ def load_library():
     lib = ctypes.CDLL(path)
     P, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
     lib.hr_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64, P]
+    lib.hr_init_with_buffers.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64,
+                                         ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.hr_check_trace.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_plain.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_kbase.argtypes = [P, u32, P, u64, u32, P]
@@ -175,7 +177,10 @@ class Checker:
     packing: tid width, 0 = 16).
     """
 
-    def __init__(self, regions, report_capacity: int = 1 << 20, stream=None):
+    def __init__(self, regions, report_capacity: int = 1 << 20, stream=None, buffers=None):
+        """``buffers``: optional caller-owned device tensors, one per region, as
+        ``shadow`` or ``(shadow, ring)`` (ring may be None); they must stay alive
+        and untouched while the checker lives (hr_init_with_buffers)."""
         self._lib = load_library()
         arr = (HrRegionDesc * len(regions))()
         for i, r in enumerate(regions):
@@ -190,7 +195,25 @@ class Checker:
         self.regions = [dict(r) for r in regions]
         self.report_capacity = report_capacity
         ctx = ctypes.c_void_p()
-        rc = self._lib.hr_init(ctypes.byref(ctx), arr, len(regions), report_capacity, _stream_handle(stream))
+        self._buffers = None
+        if buffers is None:
+            rc = self._lib.hr_init(ctypes.byref(ctx), arr, len(regions), report_capacity, _stream_handle(stream))
+        else:
+            if len(buffers) != len(regions):
+                raise ValueError("one buffer entry per region")
+            pairs = [b if isinstance(b, (tuple, list)) else (b, None) for b in buffers]
+            for i, (sh, ring) in enumerate(pairs):
+                need = int(regions[i]["n_words"]) * (4 if int(regions[i].get("shadow_bytes", 8)) == 4 else 8)
+                if not sh.is_cuda or sh.numel() * sh.element_size() < need:
+                    raise ValueError("shadow buffer %d must be a device tensor of >= %d bytes" % (i, need))
+                cap = int(regions[i].get("report_capacity", 0)) or report_capacity
+                if ring is not None and (not ring.is_cuda or ring.numel() * ring.element_size() < 16 * cap):
+                    raise ValueError("ring buffer %d must be a device tensor of >= %d bytes" % (i, 16 * cap))
+            sh_arr = (ctypes.c_void_p * len(pairs))(*[sh.data_ptr() for sh, _ in pairs])
+            ring_arr = (ctypes.c_void_p * len(pairs))(*[(r.data_ptr() if r is not None else None) for _, r in pairs])
+            self._buffers = pairs   # keep the tensors alive with the context
+            rc = self._lib.hr_init_with_buffers(ctypes.byref(ctx), arr, len(regions), report_capacity, sh_arr,
+                                                ring_arr, _stream_handle(stream))
         if rc:
             raise HiRaceError(rc, "hr_init")
         self._ctx = ctx

@@ -150,3 +150,27 @@ def test_batch_mixes_shadow_sizes(oracle_mod, hr):
     for (races, status, n_total, _), (tr, info) in zip(got, [(t1, i1), (t2, i2)]):
         assert status == hr.HR_OK
         assert hr.race_keys(races) == oracle_mod.race_keys(oracle_mod.bruteforce(tr, 256, 32))
+
+
+@pytest.mark.parametrize("shadow_bytes", [8, 4])
+def test_caller_owned_buffers(oracle_mod, hr, shadow_bytes):
+    """hr_init_with_buffers: the checker works in tensors the caller allocated,
+    finds the oracle's races, and leaves the tensors to the caller."""
+    import torch
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 3), inject=True, n_blocks=8)
+    n = info["n_words"]
+    shadow = torch.full((n * shadow_bytes // 4,), -1, dtype=torch.int32, device="cuda")  # garbage: init clears it
+    ring = torch.zeros((1 << 16) * 4, dtype=torch.int32, device="cuda")
+    reg = dict(n_words=n, block_dim=256, shadow_bytes=shadow_bytes, tid_bits=18 if shadow_bytes == 4 else 0,
+               report_capacity=1 << 16)
+    ck = hr.Checker([reg], buffers=[(shadow, ring)])
+    ck.check_trace(0, to_dev(tr))
+    races, status, n_total, _ = ck.report(0)
+    ck.close()
+    assert status == hr.HR_OK
+    assert hr.race_keys(races) == oracle_mod.race_keys(oracle_mod.bruteforce(tr, 256, 32))
+    torch.cuda.synchronize()
+    assert int((shadow != 0).sum()) > 0            # the checker's state lives in the caller's tensor
+    shadow.zero_()                                   # still the caller's to use after hr_destroy
+    ring.zero_()
+    torch.cuda.synchronize()

@@ -96,3 +96,21 @@ def test_count_form_equals_pairwise(oracle_mod):
     # the public entry point switches forms by group size
     tr = tg.build_trace(C.random_program(np.random.default_rng(9), 64, 8, 2, 2000, 2, 1))
     assert O.race_keys(O.bruteforce(tr, 8, 4, pair_limit=1)) == O.race_keys(O.bruteforce(tr, 8, 4))
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_word_partitioned_serial_fsm_equals_serial(oracle_mod, threads):
+    """Word-range partitions run the same per-word FSM: identical report set."""
+    from paper_2401_04701_gb300 import tracegen as tg
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 4), inject=True, n_blocks=4)
+    a = oracle_mod.serial_fsm(tr, info["block_dim"], info["n_words"])
+    b = oracle_mod.serial_fsm_parallel(tr, info["block_dim"], info["n_words"], threads=threads)
+    key = lambda r: {(int(k), int(w), int(e), int(t), int(o))
+                     for k, w, e, t, o in zip(r["kernel"], r["word"], r["epoch"], r["tid"], r["op"])}
+    assert len(a) == len(b) and key(a) == key(b)
+    rng = np.random.default_rng(7)
+    cases = C.random_cases(rng, 3000, 6, C.PHASES4)
+    tr = C.combined_trace(cases, C.PHASES4)
+    a = oracle_mod.serial_fsm(tr, C.TOY_BLOCK_DIM, len(cases), C.TOY_WARP)
+    b = oracle_mod.serial_fsm_parallel(tr, C.TOY_BLOCK_DIM, len(cases), C.TOY_WARP, threads=threads)
+    assert key(a) == key(b)
