@@ -181,10 +181,14 @@ def instrumented_slowdown(dev, reps=20):
     keys = torch.randint(0, n_bins, (n,), device=dev, dtype=torch.int32)
     bins = torch.zeros(n_bins, dtype=torch.int32, device=dev)
     red = torch.rand(n, device=dev)
+    sums = torch.zeros(n // 256, device=dev)
     jobs = {
         "stencil": (2 * n, lambda v: hirace.run_stencil(v, d_in, d_out)),
         "histogram": (n_bins, lambda v: hirace.run_histogram(v, keys, bins)),
         "reduction": (n, lambda v: hirace.run_reduce(v, red)),
+        # block reduction in __shared__ memory, its shadow in HBM or beside it in shared memory
+        "shared_reduction_hbm_shadow": (n, lambda v: hirace.run_smem_reduce(v, d_in, sums, 0 if v is None else 1)),
+        "shared_reduction_smem_shadow": (n, lambda v: hirace.run_smem_reduce(v, d_in, sums, 0 if v is None else 2)),
     }
     out = {}
     stream = torch.cuda.current_stream(dev)

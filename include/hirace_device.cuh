@@ -334,6 +334,71 @@ static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long
     hr_set_error(v.error, HR_ERR_CONTENTION);
 }
 
+/* ---------------------------------------------------------------------------
+ * Shadow in shared memory for a block's __shared__ array
+ *
+ * A __shared__ array belongs to one block, so only that block's threads can
+ * touch it and its shadow can live beside it in shared memory: the FSM step is
+ * the same (thread relations never reach "other block"), the CAS is a
+ * shared-memory atomic, and the shadow is fresh in every launch.  Races go to
+ * the region's report ring with word = block index * n_words + word, the
+ * numbering a trace of the same kernel uses for per-block arrays.
+ * ------------------------------------------------------------------------- */
+typedef struct hr_smem_view {
+    unsigned long long* shadow; /* n_words shadow values in this block's shared memory */
+    uint32_t n_words;           /* monitored words of the block's array */
+    uint32_t word_base;         /* this block's first word in race reports */
+} hr_smem_view;
+
+/* Every thread of the block calls this before its first monitored access:
+ * zeroes the shadow `buf` (n_words values in shared memory) and waits for the
+ * whole block (a barrier that precedes all monitored accesses, so it orders
+ * nothing the checker sees). */
+static __device__ __forceinline__ hr_smem_view hr_smem_begin(unsigned long long* buf, uint32_t n_words)
+{
+    const uint32_t nt = blockDim.x * blockDim.y * blockDim.z;
+    const uint32_t t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (uint32_t i = t; i < n_words; i += nt) buf[i] = 0ull;
+    __syncthreads();
+    hr_smem_view sv;
+    sv.shadow = buf;
+    sv.n_words = n_words;
+    sv.word_base = (blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)) * n_words;
+    return sv;
+}
+
+/* hr_access for word `word` of the block's shared array; `v` supplies the
+ * table, geometry, kernel ordinal, report ring and error word. */
+static __device__ __forceinline__ void hr_access_shared(const hr_view& v, const hr_smem_view& sv, uint32_t word,
+                                                        uint32_t op, const hr_clock& c)
+{
+    if (word >= sv.n_words || op > HR_A) {
+        hr_set_error(v.error, word >= sv.n_words ? HR_ERR_RANGE : HR_ERR_UNSUPPORTED);
+        return;
+    }
+    if (c.bc > HR_BC_MAX || c.wc > HR_WC_MAX) {
+        hr_set_error(v.error, HR_ERR_CLOCK_OVERFLOW);
+        return;
+    }
+    unsigned long long* p = sv.shadow + word;
+    const uint32_t ktag = v.kernel & 7u;
+    uint64_t o = *(volatile unsigned long long*)p;
+    for (int it = 0; it < HR_CAS_RETRY_CAP; ++it) {
+        uint32_t raced = 0;
+        const uint64_t n = hr_fsm_step(o, c.tid, op, c.bc, c.wc, ktag, v.geom, v.table, &raced);
+        if (n == o) return;
+        const uint64_t prev = atomicCAS(p, (unsigned long long)o, (unsigned long long)n);
+        if (prev == o) {
+            if (raced)
+                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, sv.word_base + word, c.tid, v.kernel, c.bc,
+                               v.region, op, raced - 1u);
+            return;
+        }
+        o = prev;
+    }
+    hr_set_error(v.error, HR_ERR_CONTENTION);
+}
+
 #endif /* __CUDACC__ */
 
 #ifdef __cplusplus

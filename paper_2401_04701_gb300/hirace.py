@@ -387,7 +387,9 @@ def load_workloads():
     lib.hrw_reduce.argtypes = [VP, P, u32, u32, i32, P]
     lib.hrw_probe.argtypes = [i32, P, u32, u32, P, u32, u32, P]
     lib.hrw_trace_probe.argtypes = [i32, P, ctypes.c_uint64, P, u32, P, u32, u32, P]
-    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce, lib.hrw_probe, lib.hrw_trace_probe):
+    lib.hrw_smem_reduce.argtypes = [VP, i32, P, P, u32, u32, i32, P]
+    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce, lib.hrw_probe, lib.hrw_trace_probe,
+              lib.hrw_smem_reduce):
         f.restype = i32
     _wl = lib
     return lib
@@ -405,6 +407,15 @@ def run_histogram(view, d_keys, d_bins, block=256, racy_stride=0, stream=None):
                                         d_keys.numel(), d_bins.data_ptr(), block, racy_stride, _stream_handle(stream))
     if rc:
         raise RuntimeError("hrw_histogram failed (%d)" % rc)
+
+
+def run_smem_reduce(view, d_in, d_out, mode, block=256, drop_level=-1, stream=None):
+    """Block reduction through a __shared__ buffer: mode 0 plain, 1 monitored
+    through the region's global shadow, 2 through a shared-memory shadow."""
+    rc = load_workloads().hrw_smem_reduce(ctypes.byref(view) if view is not None else None, mode, d_in.data_ptr(),
+                                          d_out.data_ptr(), d_in.numel(), block, drop_level, _stream_handle(stream))
+    if rc:
+        raise RuntimeError("hrw_smem_reduce failed (%d)" % rc)
 
 
 def run_reduce(view, d_data, block=256, drop_level=-1, stream=None):

@@ -384,6 +384,52 @@ def reduce_program(n: int, block: int, drop_level: int = -1) -> np.ndarray:
     return rec
 
 
+def smem_reduce_program(n: int, block: int, drop_level: int = -1) -> np.ndarray:
+    """Access program of a block reduction through a __shared__ buffer of
+    ``block`` words per block (word = block index * block + t): every thread
+    writes its word, a barrier, then at level L threads t < s = block >> (L+1)
+    read t and t+s and write t, each level followed by a barrier (except after
+    level drop_level); finally thread 0 reads word 0."""
+    grid = -(-n // block)
+    b = np.arange(grid, dtype=np.int64).reshape(-1, 1)
+    t = np.arange(block, dtype=np.int64).reshape(1, -1)
+    every_tid = (b * block + t).ravel()
+    parts = []
+
+    def add(mask, word, op, bc, step):
+        tid = np.broadcast_to(b * block + t, mask.shape)[mask]
+        w = np.broadcast_to(word, mask.shape)[mask]
+        parts.append((w, tid, np.full(len(tid), bc), np.full(len(tid), op), np.full(len(tid), step)))
+
+    full = np.ones((grid, block), bool)
+    add(full, b * block + t, OP_W, 0, 0.0)
+    bc = 1
+    parts.append((np.zeros(len(every_tid)), every_tid, np.full(len(every_tid), bc),
+                  np.full(len(every_tid), OP_SYNCTHREADS), np.full(len(every_tid), 0.5)))
+    level, s = 0, block >> 1
+    while s > 0:
+        act = np.broadcast_to(t < s, (grid, block))
+        step = 1.0 + 3 * level
+        add(act, b * block + t, OP_R, bc, step)
+        add(act, b * block + t + s, OP_R, bc, step + 1)
+        add(act, b * block + t, OP_W, bc, step + 2)
+        if level != drop_level:
+            bc += 1
+            parts.append((np.zeros(len(every_tid)), every_tid, np.full(len(every_tid), bc),
+                          np.full(len(every_tid), OP_SYNCTHREADS), np.full(len(every_tid), step + 2.5)))
+        s >>= 1
+        level += 1
+    add(np.broadcast_to(t == 0, (grid, block)), b * block, OP_R, bc, 1.0 + 3 * level)
+    word, tid, bcs, op, step = (np.concatenate([p[j] for p in parts]) for j in range(5))
+    order = np.lexsort((tid, step, bcs))
+    rec = np.zeros(len(order), RECORD)
+    rec["word"] = word[order].astype(np.int64)
+    rec["tid"] = tid[order]
+    rec["bc"] = bcs[order]
+    rec["op"] = op[order]
+    return rec
+
+
 # --------------------------------------------------------------------------
 # Workload 3: power-law graph, push-style relaxation
 # --------------------------------------------------------------------------

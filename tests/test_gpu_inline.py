@@ -105,3 +105,31 @@ def test_kernel_end_between_launches(oracle_mod, hr):
     assert status == hr.HR_OK
     got = hr.race_keys(races)
     assert got == {(k, w, e) for k in range(1, 10, 2) for (_, w, e) in want}
+
+
+@pytest.mark.parametrize("drop", [-1, 0, 3, 7])
+def test_shared_memory_shadow(oracle_mod, hr, drop):
+    """Block reduction through __shared__ memory: the shadow in shared memory
+    (hr_access_shared) and the region's global shadow (hr_access) report the
+    oracle's races on the per-block word numbering, and the sums are unchanged."""
+    import torch
+    n, block = 1 << 18, 256
+    d_in = torch.rand(n, device="cuda")
+    grid = n // block
+    want = oracle_keys(oracle_mod, tg.smem_reduce_program(n, block, drop), n)
+    if drop < 0:
+        assert not want
+    outs = []
+    for mode in (1, 2):
+        out = torch.zeros(grid, device="cuda")
+        with hr.Checker([dict(n_words=n, block_dim=block)]) as ck:
+            hr.run_smem_reduce(ck.device_view(0), d_in, out, mode, block, drop)
+            races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK
+        assert hr.race_keys(races) == want and n_total == len(want)
+        outs.append(out)
+    plain = torch.zeros(grid, device="cuda")
+    hr.run_smem_reduce(None, d_in, plain, 0, block, drop)
+    torch.cuda.synchronize()
+    if drop < 0:
+        assert torch.equal(outs[0], plain) and torch.equal(outs[1], plain)
