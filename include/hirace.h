@@ -252,6 +252,33 @@ hr_status hr_reset(hr_ctx* ctx, uint32_t region, hr_stream_t stream);
 hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_t n_words, uint32_t block_dim,
                                 uint32_t warp_size, hr_stream_t stream);
 
+/*
+ * Selective monitoring (Sec. IV-A: instrumentation can be switched on or off
+ * per thread and per address, and symmetric work groups can be represented by
+ * a few threads to save work and memory).  Accesses outside the filter are not
+ * checked and raise no error; the races reported are exactly those among the
+ * monitored accesses.
+ */
+typedef struct hr_filter {
+    uint64_t word_lo;   /* word window [word_lo, word_hi): shadow word i holds word word_lo + i, */
+    uint64_t word_hi;   /*   so the region needs only word_hi - word_lo words; word_hi 0 = no window */
+    uint32_t block_lo;  /* monitored blocks [block_lo, block_hi); block_hi 0 = every block */
+    uint32_t block_hi;
+    uint32_t lane_mask; /* monitored lanes of each warp (bit l: lane l = tid mod block_dim mod
+                           warp_size); 0xFFFFFFFF = every lane, 0 is invalid */
+    uint32_t reserved;  /* must be 0 */
+} hr_filter;
+
+/*
+ * hr_set_filter - monitor only the accesses `filter` selects, on later checks
+ * and device views of `region` (NULL: monitor everything again).  Race
+ * records keep absolute word indices.  Stream-ordered; the filter stays set
+ * across hr_reset and is cleared by hr_region_reconfigure.  HR_ERR_INVALID if
+ * the window is empty or wider than the region, block_hi < block_lo (with
+ * block_hi != 0), lane_mask is 0 or reserved is not 0.
+ */
+hr_status hr_set_filter(hr_ctx* ctx, uint32_t region, const hr_filter* filter, hr_stream_t stream);
+
 /* hr_destroy - synchronise and free everything the context owns. */
 hr_status hr_destroy(hr_ctx* ctx);
 

@@ -97,6 +97,7 @@ typedef struct hr_view {
     hr_geom geom;
     unsigned int kernel;            /* kernel ordinal of the launch being checked */
     unsigned int region;
+    hr_filter filter;               /* monitored words, blocks and lanes (hr_set_filter) */
 } hr_view;
 
 /* Thread-private clocks of an instrumented thread. */
@@ -196,6 +197,39 @@ static __device__ __forceinline__ uint32_t hr_ld_relaxed32(const unsigned int* p
 /* widths of the compact packing's clock fields */
 static __device__ __forceinline__ uint32_t hr_wc_bits(const hr_geom& g) { return (24u - g.tid_bits) >> 1; }
 static __device__ __forceinline__ uint32_t hr_bc_bits(const hr_geom& g) { return 24u - g.tid_bits - hr_wc_bits(g); }
+
+/* Whether a filter selects only part of the accesses. */
+static __device__ __forceinline__ bool hr_filter_active(const hr_filter& f)
+{
+    return f.word_hi != 0 || f.block_hi != 0 || f.lane_mask != 0xFFFFFFFFu;
+}
+
+/* Whether thread tid's access to `word` is monitored under filter f; *idx gets
+ * the shadow index of the word (word - word_lo inside a window). */
+static __device__ __forceinline__ bool hr_monitored(const hr_filter& f, const hr_geom& g, uint32_t tid,
+                                                    unsigned long long word, unsigned long long* idx)
+{
+    *idx = word;
+    if (f.word_hi != 0) {
+        if (word < f.word_lo || word >= f.word_hi) return false;
+        *idx = word - f.word_lo;
+    }
+    if (f.block_hi != 0 || f.lane_mask != 0xFFFFFFFFu) {
+        uint32_t blk, loc;
+        if (g.bd_shift != ~0u) {
+            blk = tid >> g.bd_shift;
+            loc = tid & (g.block_dim - 1u);
+        } else {
+            blk = hr_fastdiv(tid, g.bd_magic);
+            loc = tid - blk * g.block_dim;
+        }
+        const uint32_t lane = g.ws_shift != ~0u ? (loc & (g.warp_size - 1u))
+                                                : loc - hr_fastdiv(loc, g.ws_magic) * g.warp_size;
+        if (f.block_hi != 0 && (blk < f.block_lo || blk >= f.block_hi)) return false;
+        if (((f.lane_mask >> lane) & 1u) == 0) return false;
+    }
+    return true;
+}
 
 /* Whether an access's identity and clocks fit the region's packing. */
 static __device__ __forceinline__ bool hr_fits(uint32_t tid, uint32_t bc, uint32_t wc, const hr_geom& g)
@@ -308,6 +342,8 @@ static __device__ __forceinline__ void hr_syncwarp(hr_clock& c)
 static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long long word, uint32_t op,
                                                  const hr_clock& c)
 {
+    const unsigned long long abs_word = word;
+    if (hr_filter_active(v.filter) && !hr_monitored(v.filter, v.geom, c.tid, abs_word, &word)) return;
     if (word >= v.n_words || op > HR_A) {
         hr_set_error(v.error, word >= v.n_words ? HR_ERR_RANGE : HR_ERR_UNSUPPORTED);
         return;
@@ -325,7 +361,7 @@ static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long
         const uint64_t prev = hr_shadow_cas(v.shadow, word, o, n, v.geom);
         if (prev == o) {
             if (raced)
-                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)word, c.tid, v.kernel, c.bc,
+                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)abs_word, c.tid, v.kernel, c.bc,
                                v.region, op, raced - 1u);
             return;
         }

@@ -20,6 +20,7 @@ struct RegionHost {
     void* work_mem = nullptr;
     hr_work work{};
     unsigned kernel = 0;                  // kernel ordinal seen by device views
+    hr_filter filter = hr_filter_all();   // monitored accesses (hr_set_filter)
     bool owns_shadow = true;              // false: caller-owned (hr_init_with_buffers)
     bool owns_ring = true;
     cudaEvent_t done = nullptr;           // recorded after every call on the region
@@ -189,6 +190,7 @@ static hr_status init_impl(hr_ctx** out, const hr_region_desc* regions, uint32_t
         h.ring_cap = r.ring_cap;
         h.region = i;
         h.geom = hr_desc_geom(r.desc);
+        h.filter = hr_filter_all();
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_regions, hdev.data(), sizeof(hr_region_dev) * n_regions, cudaMemcpyHostToDevice, s);
@@ -434,10 +436,31 @@ extern "C" hr_status hr_region_reconfigure(hr_ctx* ctx, uint32_t region, uint64_
     r.desc.n_words = n_words;
     r.desc.block_dim = block_dim;
     r.desc.warp_size = warp_size;
+    r.filter = hr_filter_all();
     cudaError_t e = hr_launch_reconfigure(r.d, n_words, hr_desc_geom(r.desc), s);
     if (e == cudaSuccess) e = hr_launch_reset(r.d, r.shadow, n_words * hr_desc_shadow_bytes(r.desc), s);
     if (e == cudaSuccess) e = mark_done(r, s);
     r.kernel = 0;
+    return cuda_status(e);
+}
+
+extern "C" hr_status hr_set_filter(hr_ctx* ctx, uint32_t region, const hr_filter* filter, hr_stream_t stream)
+{
+    if (!valid_region(ctx, region)) return HR_ERR_INVALID;
+    RegionHost& r = ctx->regions[region];
+    const hr_filter f = filter ? *filter : hr_filter_all();
+    if (f.reserved != 0 || f.lane_mask == 0) return HR_ERR_INVALID;
+    if (f.word_hi == 0 ? f.word_lo != 0 : (f.word_hi <= f.word_lo || f.word_hi - f.word_lo > r.desc.n_words))
+        return HR_ERR_INVALID;
+    if (f.word_hi > (1ull << 32)) return HR_ERR_INVALID;  // record word indices are 32-bit
+    if (f.block_hi != 0 && f.block_hi < f.block_lo) return HR_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();  // report only errors of this call's launches
+    cudaError_t e = hr_launch_set_filter(r.d, f, s);
+    if (e == cudaSuccess) {
+        r.filter = f;
+        e = mark_done(r, s);
+    }
     return cuda_status(e);
 }
 
@@ -463,6 +486,7 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     out->n_words = r.desc.n_words;
     out->ring_cap = r.ring_cap;
     out->geom = hr_desc_geom(r.desc);
+    out->filter = r.filter;
     out->kernel = r.kernel;
     out->region = region;
     return HR_OK;

@@ -55,7 +55,16 @@ struct hr_region_dev {
     unsigned int region;
     unsigned long long counters[4];  // accesses, CAS attempts, CAS retries, merged lanes
     hr_geom geom;
+    hr_filter filter;             // monitored words, blocks, lanes (hr_set_filter)
 };
+
+// the filter that monitors every access
+__host__ __device__ inline hr_filter hr_filter_all()
+{
+    hr_filter f{};
+    f.lane_mask = 0xFFFFFFFFu;
+    return f;
+}
 
 // One job = one trace checked on one region.  A single-trace check is a batch
 // of one job; a batch interleaves the jobs' stages wave-major.
@@ -205,3 +214,4 @@ cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow,
                             cudaStream_t stream);
 cudaError_t hr_launch_reconfigure(hr_region_dev* d_region, unsigned long long n_words, hr_geom geom,
                                   cudaStream_t stream);
+cudaError_t hr_launch_set_filter(hr_region_dev* d_region, hr_filter filter, cudaStream_t stream);

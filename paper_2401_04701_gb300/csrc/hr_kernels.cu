@@ -385,7 +385,8 @@ struct Shape {
     // records, FSM table, aggregation scratch, tile infos, full/empty mbarriers,
     // tile-finish counters, per-warp geometry and diagnostics
     static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 +
-                                    2 * HR_RING * 4 + CONS * sizeof(hr_geom) + CONS * 4 * 4;
+                                    2 * HR_RING * 4 + CONS * sizeof(hr_geom) + CONS * 4 * 4 +
+                                    CONS * sizeof(hr_filter);
     static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
 };
 
@@ -660,6 +661,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     unsigned* s_fin = reinterpret_cast<unsigned*>(s_empty + HR_RING);  // [2 * HR_RING]
     hr_geom* s_geom = reinterpret_cast<hr_geom*>(s_fin + 2 * HR_RING);  // [HR_CONSUMERS]
     unsigned* s_cnt = reinterpret_cast<unsigned*>(s_geom + HR_CONSUMERS);  // [HR_CONSUMERS][4]
+    hr_filter* s_filt = reinterpret_cast<hr_filter*>(s_cnt + 4 * HR_CONSUMERS);  // [HR_CONSUMERS]
 
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
@@ -684,6 +686,8 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     hr_region_dev* region = nullptr;
     // the region's geometry lives in this warp's shared slot (read per use, not held in registers)
     const hr_geom& g = s_geom[wid];
+    const hr_filter& filt = s_filt[wid];
+    bool filtering = false;  // the region's filter selects only part of the accesses
     unsigned long long* shadow = nullptr;
     unsigned long long n_words = 0;
     Acc* my_acc = s_acc + (size_t)wid * HR_RPL * 32;
@@ -744,8 +748,12 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             flush();
             cur = t_region;
             region = regions + cur;
-            if (lane == 0) s_geom[wid] = region->geom;
+            if (lane == 0) {
+                s_geom[wid] = region->geom;
+                s_filt[wid] = region->filter;
+            }
             __syncwarp();
+            filtering = hr_filter_active(filt);
             shadow = region->shadow;
             n_words = region->n_words;
         }
@@ -797,20 +805,29 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 // record key (kernel + kernel base, bc, wc) against the wave's
                 const bool same_wave = v.z == bcwc && (v.w & 0xFFFFu) + kb == kern;
                 bool a = in && op <= HR_A;
+                // selective monitoring: unmonitored accesses are skipped, a word window
+                // maps words to shadow indices
+                unsigned widx = v.x;
+                bool mon = true;
+                if (filtering && a && same_wave) {
+                    unsigned long long ix = v.x;
+                    mon = hr_monitored(filt, g, v.y, v.x, &ix);
+                    widx = (unsigned)ix;
+                }
                 if (in) {
                     if (!same_wave) err = HR_ERR_ORDER;
                     else if (op > HR_SYNCWARP || (op == HR_SYNCWARP && (flags & HR_RECFLAG_PARTIAL_MASK)))
                         err = HR_ERR_UNSUPPORTED;
-                    else if (a && v.x >= n_words)
+                    else if (a && mon && widx >= n_words)
                         err = HR_ERR_RANGE;
                 }
-                if (a && same_wave && v.x < n_words && !hr_fits(v.y, bc, wc, g)) {
+                a = a && same_wave && mon && widx < n_words;
+                if (a && !hr_fits(v.y, bc, wc, g)) {
                     err = HR_ERR_CLOCK_OVERFLOW;  // tid, bc or wc wider than the shadow packing
                     a = false;
                 }
-                a = a && same_wave && v.x < n_words;
                 act[k] = a;
-                word[k] = v.x;
+                word[k] = widx;
                 tidv[k] = v.y;
                 opv[k] = op;
                 grp[k] = 1u << lane;
@@ -911,7 +928,8 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 if (done && raced[k]) {
                     const unsigned rt = who[k] == lane ? tidv[k] : my_acc[k * 32 + who[k]].tid;
                     const unsigned ro = who[k] == lane ? opv[k] : my_acc[k * 32 + who[k]].op;
-                    hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, word[k], rt,
+                    const unsigned abs_word = word[k] + (filtering ? (unsigned)filt.word_lo : 0u);
+                    hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, abs_word, rt,
                                    kern, bc, region->region, ro, raced[k] - 1u);
                 }
             }
@@ -952,7 +970,10 @@ __global__ void hr_reconfigure_state(hr_region_dev* region, unsigned long long n
 {
     region->n_words = n_words;
     region->geom = geom;
+    region->filter = hr_filter_all();
 }
+
+__global__ void hr_set_filter_state(hr_region_dev* region, hr_filter filter) { region->filter = filter; }
 
 int g_grid[HR_N_VARIANTS] = {};
 
@@ -1054,6 +1075,12 @@ cudaError_t hr_launch_reconfigure(hr_region_dev* d_region, unsigned long long n_
                                   cudaStream_t stream)
 {
     hr_reconfigure_state<<<1, 1, 0, stream>>>(d_region, n_words, geom);
+    return cudaGetLastError();
+}
+
+cudaError_t hr_launch_set_filter(hr_region_dev* d_region, hr_filter filter, cudaStream_t stream)
+{
+    hr_set_filter_state<<<1, 1, 0, stream>>>(d_region, filter);
     return cudaGetLastError();
 }
 

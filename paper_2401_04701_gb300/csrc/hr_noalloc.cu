@@ -78,6 +78,7 @@ __global__ void hr_noalloc_begin(hr_region_dev* region, unsigned long long* shad
     region->region = 0;
     for (int i = 0; i < 4; ++i) region->counters[i] = 0;
     region->geom = geom;
+    region->filter = hr_filter_all();
 }
 
 __global__ void hr_noalloc_end(const hr_region_dev* region, hr_result* result)

@@ -40,6 +40,12 @@ class HrGeom(ctypes.Structure):
                 ("shadow_bytes", ctypes.c_uint32), ("tid_bits", ctypes.c_uint32)]
 
 
+class HrFilter(ctypes.Structure):
+    """Mirror of hr_filter (include/hirace.h): selective monitoring."""
+    _fields_ = [("word_lo", ctypes.c_uint64), ("word_hi", ctypes.c_uint64), ("block_lo", ctypes.c_uint32),
+                ("block_hi", ctypes.c_uint32), ("lane_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
 class HrJob(ctypes.Structure):
     _fields_ = [("region", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("trace", ctypes.c_void_p),
                 ("n", ctypes.c_uint64)]
@@ -50,10 +56,10 @@ class HrView(ctypes.Structure):
     _fields_ = [("shadow", ctypes.c_void_p), ("ring", ctypes.c_void_p), ("n_races", ctypes.c_void_p),
                 ("error", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("table", ctypes.c_void_p),
                 ("n_words", ctypes.c_uint64), ("ring_cap", ctypes.c_uint64), ("geom", HrGeom),
-                ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32)]
+                ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32), ("filter", HrFilter)]
 
 
-assert ctypes.sizeof(HrView) == 112
+assert ctypes.sizeof(HrView) == 144
 
 
 class HiRaceError(RuntimeError):
@@ -79,6 +85,7 @@ def load_library():
     lib.hr_init.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64, P]
     lib.hr_init_with_buffers.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64,
                                          ctypes.POINTER(P), ctypes.POINTER(P), P]
+    lib.hr_set_filter.argtypes = [P, u32, ctypes.POINTER(HrFilter), P]
     lib.hr_check_trace.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_plain.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_kbase.argtypes = [P, u32, P, u64, u32, P]
@@ -289,6 +296,17 @@ class Checker:
         v = HrView()
         self._check(self._lib.hr_device_view(self._ctx, region, ctypes.byref(v)), "hr_device_view")
         return v
+
+    def set_filter(self, region: int, word_lo: int = 0, word_hi: int = 0, block_lo: int = 0, block_hi: int = 0,
+                   lane_mask: int = 0xFFFFFFFF, stream=None):
+        """Monitor only words [word_lo, word_hi) (word_hi 0: all), blocks
+        [block_lo, block_hi) (block_hi 0: all) and the lanes in lane_mask."""
+        f = HrFilter(word_lo, word_hi, block_lo, block_hi, lane_mask, 0)
+        self._check(self._lib.hr_set_filter(self._ctx, region, ctypes.byref(f), _stream_handle(stream)),
+                    "hr_set_filter")
+
+    def clear_filter(self, region: int, stream=None):
+        self._check(self._lib.hr_set_filter(self._ctx, region, None, _stream_handle(stream)), "hr_set_filter")
 
     def set_variant(self, variant: int):
         self._check(self._lib.hr_set_variant(self._ctx, variant), "hr_set_variant")
