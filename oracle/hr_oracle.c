@@ -353,6 +353,132 @@ int64_t hro_bruteforce(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_
     return nr;
 }
 
+/* --------------------------------------- every racy epoch (report mode 1) */
+
+/* Rows for one (kernel, word) group: one per distinct epoch e = max(bc_a, bc_b)
+ * over its racy pairs (a, b).  ops_mask of a row: the ops of the accesses that
+ * complete such a pair (the later one of the pair in wave order, and both when
+ * they share a wave).  `ops` is a zeroed scratch of 65536 entries, zeroed again
+ * on return. */
+static int64_t emit_epochs(const hro_rec* r0, uint8_t* ops, uint8_t* form_of, uint8_t form, hro_race* out,
+                           uint64_t cap, int64_t nr)
+{
+    for (uint32_t e = 0; e < 65536; e++) {
+        if (!ops[e]) continue;
+        if ((uint64_t)nr < cap) {
+            hro_race* o = &out[nr];
+            memset(o, 0, sizeof *o);
+            o->word = r0->word;
+            o->kernel = r0->kernel;
+            o->epoch = (uint16_t)e;
+            o->ops_mask = ops[e];
+            o->kinds_mask = 0xFF;
+            o->method = form;
+        }
+        nr++;
+        ops[e] = 0;
+    }
+    (void)form_of;
+    return nr;
+}
+
+static void epochs_pairwise(const hro_rec* r, const uint64_t* g, uint64_t m, uint32_t bd, uint32_t ws,
+                            uint8_t* ops)
+{
+    for (uint64_t i = 0; i < m; i++)
+        for (uint64_t j = i + 1; j < m; j++) {
+            const hro_rec* a = &r[g[i]];
+            const hro_rec* b = &r[g[j]];  /* g is in wave order: b is not earlier than a */
+            if (a->tid == b->tid || !conflicting(a->op, b->op) || !concurrent(a, b, bd, ws)) continue;
+            uint16_t e = a->bc > b->bc ? a->bc : b->bc;
+            ops[e] |= (uint8_t)(1u << b->op);
+            if (wave_of(a) == wave_of(b)) ops[e] |= (uint8_t)(1u << a->op);
+        }
+}
+
+/* The count form of epochs_pairwise: every wave, not only up to the first racy one. */
+static void epochs_counts(const hro_rec* r, const uint64_t* g, uint64_t m, uint32_t bd, uint32_t ws,
+                          uint8_t* ops)
+{
+    hmap mb, mbbc, mwbc, mww, mtw;
+    hm_init(&mb, m); hm_init(&mbbc, m); hm_init(&mwbc, m); hm_init(&mww, m); hm_init(&mtw, m);
+    int32_t total[3] = {0, 0, 0};
+    uint32_t wpb = (bd + ws - 1) / ws;
+    uint64_t s = 0;
+    while (s < m) {
+        uint64_t e = s;
+        uint64_t wv = wave_of(&r[g[s]]);
+        while (e < m && wave_of(&r[g[e]]) == wv) e++;
+        for (uint64_t q = s; q < e; q++) {
+            const hro_rec* x = &r[g[q]];
+            uint64_t blk = x->tid / bd;
+            uint64_t gw = blk * wpb + (x->tid % bd) / ws;
+            total[x->op]++;
+            hm_get(&mb, blk)[x->op]++;
+            hm_get(&mbbc, (blk << 16) | x->bc)[x->op]++;
+            hm_get(&mwbc, (gw << 16) | x->bc)[x->op]++;
+            hm_get(&mww, (gw << 32) | ((uint64_t)x->bc << 16) | x->wc)[x->op]++;
+            hm_get(&mtw, ((uint64_t)x->tid << 32) | ((uint64_t)x->bc << 16) | x->wc)[x->op]++;
+        }
+        for (uint64_t q = s; q < e; q++) {
+            const hro_rec* x = &r[g[q]];
+            uint64_t blk = x->tid / bd;
+            uint64_t gw = blk * wpb + (x->tid % bd) / ws;
+            int32_t* cb = hm_get(&mb, blk);
+            int32_t* cbbc = hm_get(&mbbc, (blk << 16) | x->bc);
+            int32_t* cwbc = hm_get(&mwbc, (gw << 16) | x->bc);
+            int32_t* cww = hm_get(&mww, (gw << 32) | ((uint64_t)x->bc << 16) | x->wc);
+            int32_t* ctw = hm_get(&mtw, ((uint64_t)x->tid << 32) | ((uint64_t)x->bc << 16) | x->wc);
+            for (uint8_t c = 0; c < 3; c++) {
+                if (!conflicting(c, x->op)) continue;
+                if (total[c] - cb[c] > 0 || cbbc[c] - cwbc[c] > 0 || cww[c] - ctw[c] > 0) {
+                    ops[x->bc] |= (uint8_t)(1u << x->op);
+                    break;
+                }
+            }
+        }
+        s = e;
+    }
+    hm_free(&mb); hm_free(&mbbc); hm_free(&mwbc); hm_free(&mww); hm_free(&mtw);
+}
+
+/* Every racy (kernel, word, epoch) of a validated trace, sorted by (kernel,
+ * word, epoch): the report set when RACE is not absorbing.  Groups larger
+ * than pair_limit use the count form.  Returns the row count (may exceed
+ * cap; only cap rows are written). */
+int64_t hro_bruteforce_epochs(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_t warp_size,
+                              uint64_t pair_limit, hro_race* out, uint64_t cap)
+{
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; i++) m += is_access(r[i].op);
+    uint64_t* key = (uint64_t*)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint64_t* idx = (uint64_t*)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint8_t* ops = (uint8_t*)calloc(65536, 1);
+    uint64_t j = 0;
+    for (uint64_t i = 0; i < n; i++)
+        if (is_access(r[i].op)) {
+            key[j] = ((uint64_t)r[i].kernel << 32) | r[i].word;
+            idx[j] = i;
+            j++;
+        }
+    radix_sort(key, idx, m, 48);
+    int64_t nr = 0;
+    uint64_t s = 0;
+    while (s < m) {
+        uint64_t e = s + 1;
+        while (e < m && key[e] == key[s]) e++;
+        const int counts = e - s > pair_limit;
+        if (counts)
+            epochs_counts(r, idx + s, e - s, block_dim, warp_size, ops);
+        else
+            epochs_pairwise(r, idx + s, e - s, block_dim, warp_size, ops);
+        nr = emit_epochs(&r[idx[s]], ops, NULL, (uint8_t)counts, out, cap, nr);
+        s = e;
+    }
+    free(key); free(idx); free(ops);
+    return nr;
+}
+
 /* Force one group through a chosen form (for cross-checking the two forms). */
 int hro_group_check(const hro_rec* r, const uint64_t* g, uint64_t m, uint32_t block_dim,
                     uint32_t warp_size, int use_counts, hro_race* out)

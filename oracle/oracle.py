@@ -8,6 +8,8 @@ trace record layout on its own.
 * ``validate``     - clocks recomputed from each thread's barrier records.
 * ``bruteforce``   - the race definition (Sec. II-A, II-B), every pair of
                      accesses per (kernel, word); C code in ``hr_oracle.c``.
+                     ``bruteforce_epochs`` keeps every racy epoch of a word
+                     instead of the first (the non-absorbing report mode).
 * ``serial_fsm``   - a serial restatement of the parallel FSM (Sec. III,
                      Algorithm 1) in C, one record at a time;
                      ``serial_fsm_parallel`` runs it on disjoint word ranges,
@@ -69,6 +71,8 @@ def _lib():
         lib.hro_validate.restype = ctypes.c_int
         lib.hro_bruteforce.argtypes = [P, u64, u32, u32, u64, P, u64]
         lib.hro_bruteforce.restype = i64
+        lib.hro_bruteforce_epochs.argtypes = [P, u64, u32, u32, u64, P, u64]
+        lib.hro_bruteforce_epochs.restype = i64
         lib.hro_group_check.argtypes = [P, P, u64, u32, u32, ctypes.c_int, P]
         lib.hro_group_check.restype = ctypes.c_int
         lib.hro_serial_fsm.argtypes = [P, u64, u32, u32, u64, P, u64, P]
@@ -111,6 +115,23 @@ def bruteforce(trace, block_dim: int, warp_size: int = 32, pair_limit: int = 409
     while True:
         out = np.zeros(cap, RACE_DT)
         n = _lib().hro_bruteforce(_ptr(rec), len(rec), block_dim, warp_size, pair_limit, _ptr(out), cap)
+        if n <= cap:
+            return out[:n]
+        cap = int(n)
+
+
+def bruteforce_epochs(trace, block_dim: int, warp_size: int = 32, pair_limit: int = 4096) -> np.ndarray:
+    """Every racy (kernel, word, epoch): one row per distinct epoch max(bc_a, bc_b)
+    over the racy pairs of each (kernel, word), sorted by (kernel, word, epoch).
+    The report set of the every-epoch mode (RACE not absorbing)."""
+    rec = _as_records(trace)
+    rc, idx = validate(rec)
+    if rc:
+        raise ValueError("invalid trace: %s at record %d" % (VALIDATE_ERRORS[rc], idx))
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, RACE_DT)
+        n = _lib().hro_bruteforce_epochs(_ptr(rec), len(rec), block_dim, warp_size, pair_limit, _ptr(out), cap)
         if n <= cap:
             return out[:n]
         cap = int(n)
@@ -192,8 +213,9 @@ def race_keys(arr) -> set:
 # Pure-Python happens-before statement of the definition (tiny traces only)
 # ---------------------------------------------------------------------------
 
-def hb_races(trace, block_dim: int, warp_size: int = 32):
-    """{(kernel, word): (epoch, ops)} computed from happens-before reachability.
+def hb_races(trace, block_dim: int, warp_size: int = 32, every_epoch: bool = False):
+    """{(kernel, word): epoch} computed from happens-before reachability (with
+    every_epoch: the set of (kernel, word, epoch) over all racy pairs).
 
     Happens-before (Sec. II-A) is the transitive closure of
     * program order of each thread (its records in trace order), and
@@ -277,7 +299,12 @@ def hb_races(trace, block_dim: int, warp_size: int = 32):
             if wi != wj or ki != kj or ti == tj or not conflict(oi, oj) or ordered(i, j):
                 continue
             e = max(bc_of[i], bc_of[j])
+            if every_epoch:
+                best[(ki, wi, e)] = e
+                continue
             cur = best.get((ki, wi))
             if cur is None or e < cur:
                 best[(ki, wi)] = e
+    if every_epoch:
+        return set(best)
     return {key: e for key, e in best.items()}

@@ -114,3 +114,59 @@ def test_word_partitioned_serial_fsm_equals_serial(oracle_mod, threads):
     a = oracle_mod.serial_fsm(tr, C.TOY_BLOCK_DIM, len(cases), C.TOY_WARP)
     b = oracle_mod.serial_fsm_parallel(tr, C.TOY_BLOCK_DIM, len(cases), C.TOY_WARP, threads=threads)
     assert key(a) == key(b)
+
+
+# --------------------------------------------- every racy epoch (report mode 1)
+
+def test_every_epoch_hand_built(oracle_mod):
+    """Two blocks race in epoch 0 and again in epoch 1 (blocks are never ordered);
+    two lanes of one warp race in epoch 0 only (the barrier orders what follows)."""
+    O = oracle_mod
+    cross = [{0: [("W", 0), ("ST",), ("W", 0)], 4: [("R", 0), ("ST",)]}]
+    tr = tg.build_trace(cross)
+    assert O.race_keys(O.bruteforce_epochs(tr, 4, 2)) == {(0, 0, 0), (0, 0, 1)}
+    assert O.race_keys(O.bruteforce(tr, 4, 2)) == {(0, 0, 0)}
+    local = [{0: [("W", 0), ("ST",), ("R", 0)], 1: [("W", 0), ("ST",)]}]
+    tr = tg.build_trace(local)
+    assert O.race_keys(O.bruteforce_epochs(tr, 4, 2)) == {(0, 0, 0)}
+    later = [{0: [("R", 0), ("ST",), ("W", 0)], 1: [("R", 0), ("ST",), ("R", 0)]}]
+    tr = tg.build_trace(later)  # reads race-free in epoch 0, W/R of two lanes in epoch 1
+    assert O.race_keys(O.bruteforce_epochs(tr, 4, 2)) == {(0, 0, 1)}
+    assert O.race_keys(O.bruteforce(tr, 4, 2)) == {(0, 0, 1)}
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_every_epoch_equals_happens_before(oracle_mod, seed):
+    """The every-epoch brute force against reachability; its first epoch per
+    word is the absorbing report set."""
+    O = oracle_mod
+    rng = np.random.default_rng(300 + seed)
+    for _ in range(60):
+        bd = int(rng.choice([2, 3, 4, 6]))
+        ws = int(rng.choice([1, 2, 4]))
+        kernels = C.random_program(rng, n_threads=int(rng.integers(2, 9)), block_dim=bd, n_words=3,
+                                   n_acc=int(rng.integers(1, 12)), n_st=int(rng.integers(0, 4)),
+                                   n_sw=int(rng.integers(0, 3)), n_kernels=int(rng.integers(1, 3)))
+        tr = tg.build_trace(kernels)
+        ep = O.race_keys(O.bruteforce_epochs(tr, bd, ws))
+        assert ep == O.hb_races(tr, bd, ws, every_epoch=True)
+        first = {}
+        for k, w, e in ep:
+            first[(k, w)] = min(e, first.get((k, w), e))
+        assert {(k, w, e) for (k, w), e in first.items()} == O.race_keys(O.bruteforce(tr, bd, ws))
+
+
+def test_every_epoch_count_form_equals_pairwise(oracle_mod):
+    O = oracle_mod
+    rng = np.random.default_rng(77)
+    cases = C.random_cases(rng, 4000, 8, C.PHASES4)
+    tr = C.combined_trace(cases, C.PHASES4)
+    a = O.bruteforce_epochs(tr, C.TOY_BLOCK_DIM, C.TOY_WARP)
+    b = O.bruteforce_epochs(tr, C.TOY_BLOCK_DIM, C.TOY_WARP, pair_limit=1)
+    assert O.race_keys(a) == O.race_keys(b)
+    assert (a["ops_mask"] == b["ops_mask"]).all()
+    # injected cross-block writes race with reads of later epochs too: more rows than racy words
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 7), inject=True, n_blocks=4)
+    a = O.bruteforce_epochs(tr, info["block_dim"])
+    b = O.bruteforce_epochs(tr, info["block_dim"], pair_limit=1)
+    assert O.race_keys(a) == O.race_keys(b) and len(a) > len(O.bruteforce(tr, info["block_dim"]))
