@@ -44,6 +44,8 @@ typedef enum hr_status {
 } hr_status;
 
 /* hr_report flag bits */
+#define HR_REPORT_FIRST 0u
+#define HR_REPORT_EVERY_EPOCH 1u
 #define HR_FLAG_TRUNCATED 1u /* more races than the report ring holds; n_total stays exact */
 
 /* memory space of a region (informational: the shadow always lives in HBM) */
@@ -112,7 +114,11 @@ typedef struct hr_region_desc {
     uint8_t shadow_bytes;     /* bytes per shadow word: 8 (0 = default) or 4 (compact packing) */
     uint8_t tid_bits;         /* compact packing only: tid field width, 4..22 (0 = 16); bc and wc
                                  share the other 24 - tid_bits bits (hirace_device.cuh) */
-    uint16_t reserved;        /* must be 0 */
+    uint8_t report_mode;      /* HR_REPORT_FIRST (0): one report per racy word and kernel, the
+                                 first racy epoch (RACE absorbing); HR_REPORT_EVERY_EPOCH (1): one
+                                 per racy (word, kernel, epoch), 24 shadow bytes per word, 8-byte
+                                 packing only */
+    uint8_t reserved;         /* must be 0 */
     uint64_t report_capacity; /* race records kept for this region; 0 = the hr_init default */
 } hr_region_desc;
 

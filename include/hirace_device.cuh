@@ -80,8 +80,10 @@ typedef struct hr_geom {
     uint64_t ws_magic;
     uint32_t bd_shift;     /* log2(block_dim) when block_dim and warp_size are both powers of two, else ~0u */
     uint32_t ws_shift;     /* log2(warp_size) in that case */
-    uint32_t shadow_bytes; /* 8, or 4 for the compact packing */
+    uint32_t shadow_bytes; /* shadow bytes per word: 8, 4 (compact packing) or 24 (every-epoch mode) */
     uint32_t tid_bits;     /* compact packing: width of the tid field (4..22) */
+    uint32_t report_mode;  /* HR_REPORT_FIRST or HR_REPORT_EVERY_EPOCH */
+    uint32_t pad;
 } hr_geom;
 
 /* Everything an instrumented kernel needs for one region; pass by value. */
@@ -304,6 +306,133 @@ static __device__ __forceinline__ void hr_append_race(hr_race* ring, unsigned lo
 }
 
 /* ---------------------------------------------------------------------------
+ * Every-epoch reporting (report mode HR_REPORT_EVERY_EPOCH)
+ *
+ * The first-race FSM stops at RACE; this mode keeps checking and reports each
+ * (word, kernel, epoch) in which some access completes a racy pair.  Deciding
+ * that exactly for every later access needs, for each of the two conflict
+ * kinds (bit 0: reads and writes; bit 1: atomics and writes), where the
+ * accesses holding it sit: a later access conflicts with bit b's holders when
+ * one of them is in another block, or in its block and epoch but another
+ * warp, or in its warp and sub-epoch but another thread (Sec. II-B).  So each
+ * bit gets its own 8-byte summary, the narrowest scope holding all its
+ * accessors of the latest epoch plus that epoch's clocks:
+ *     bits 63..59 level (0 none, 1 thread, 2 warp, 3 block, 4 grid)
+ *     bits 58..56 kernel tag, 55..40 bc, 39..32 wc,
+ *     bits 31..0  the thread, the warp's first thread or the block's first thread
+ * A word's shadow is three 8-byte values in three arrays of n_words values
+ * (24 bytes per word): the bit-0 summary, the bit-1 summary, and 1 + (kernel
+ * << 16 | epoch) of the last epoch reported.  An access updates the summaries
+ * of the bits it holds (CAS), then - after a sequentially consistent fence,
+ * so that of two concurrent conflicting accesses at least one sees the other
+ * - reads the summaries of the bits it conflicts with.
+ * ------------------------------------------------------------------------- */
+#define HR_EP_NONE 0u
+#define HR_EP_THREAD 1u
+#define HR_EP_WARP 2u
+#define HR_EP_BLOCK 3u
+#define HR_EP_GRID 4u
+
+static __device__ __forceinline__ uint64_t hr_ep_pack(uint32_t lvl, uint32_t ktag, uint32_t bc, uint32_t wc,
+                                                      uint32_t who)
+{
+    return ((uint64_t)lvl << HR_SH_STATE_SHIFT) | ((uint64_t)ktag << HR_SH_KTAG_SHIFT) |
+           ((uint64_t)bc << HR_SH_BC_SHIFT) | ((uint64_t)wc << HR_SH_WC_SHIFT) | who;
+}
+
+static __device__ __forceinline__ uint32_t hr_ep_level(uint64_t s, uint32_t ktag)
+{
+    const uint32_t lvl = (uint32_t)(s >> HR_SH_STATE_SHIFT);
+    return (lvl != HR_EP_NONE && (uint32_t)((s >> HR_SH_KTAG_SHIFT) & 7u) != ktag) ? HR_EP_NONE : lvl;
+}
+
+/* Summary of one conflict bit after adding an access of thread tid at (bc, wc). */
+static __device__ __forceinline__ uint64_t hr_ep_update(uint64_t s, uint32_t tid, uint32_t bc, uint32_t wc,
+                                                        uint32_t ktag, const hr_geom& g)
+{
+    const uint32_t lvl = hr_ep_level(s, ktag);
+    if (lvl == HR_EP_NONE) return hr_ep_pack(HR_EP_THREAD, ktag, bc, wc, tid);
+    if (lvl == HR_EP_GRID) return s;
+    const uint32_t rel = hr_thread_rel(tid, (uint32_t)s, g);
+    if (rel == HR_TREL_GRID) return hr_ep_pack(HR_EP_GRID, ktag, 0, 0, 0);
+    const uint32_t obc = (uint32_t)(s >> HR_SH_BC_SHIFT) & 0xFFFFu;
+    if (obc != bc) return hr_ep_pack(HR_EP_THREAD, ktag, bc, wc, tid);  // a later epoch of the block
+    if (lvl == HR_EP_BLOCK) return s;
+    uint32_t wh, bh;
+    hr_scope_heads(tid, g, &wh, &bh);
+    if (rel == HR_TREL_BLOCK) return hr_ep_pack(HR_EP_BLOCK, ktag, bc, 0, bh);
+    const uint32_t owc = (uint32_t)(s >> HR_SH_WC_SHIFT) & 0xFFu;
+    if (owc != wc) return hr_ep_pack(HR_EP_THREAD, ktag, bc, wc, tid);  // a later sub-epoch of the warp
+    if (lvl == HR_EP_WARP || rel == HR_TREL_SAME) return s;
+    return hr_ep_pack(HR_EP_WARP, ktag, bc, wc, wh);
+}
+
+/* Whether a conflict bit's holders (summary s) include an access unordered with
+ * an access of thread tid at (bc, wc) from another thread. */
+static __device__ __forceinline__ bool hr_ep_pred(uint64_t s, uint32_t tid, uint32_t bc, uint32_t wc, uint32_t ktag,
+                                                  const hr_geom& g)
+{
+    const uint32_t lvl = hr_ep_level(s, ktag);
+    if (lvl == HR_EP_NONE) return false;
+    if (lvl == HR_EP_GRID) return true;
+    const uint32_t rel = hr_thread_rel(tid, (uint32_t)s, g);
+    if (rel == HR_TREL_GRID) return true;
+    if (((uint32_t)(s >> HR_SH_BC_SHIFT) & 0xFFFFu) != bc) return false;  // earlier epochs of its block
+    if (lvl == HR_EP_BLOCK || rel == HR_TREL_BLOCK) return true;
+    if (((uint32_t)(s >> HR_SH_WC_SHIFT) & 0xFFu) != wc) return false;    // earlier sub-epochs of its warp
+    return lvl == HR_EP_WARP || rel != HR_TREL_SAME;
+}
+
+/* Apply one access in every-epoch mode to shadow index idx of a region whose
+ * three arrays start at `shadow` (stride n_words).  Reports the race under
+ * `report_word`, once per (word, kernel, epoch).  Returns 0 or
+ * HR_ERR_CONTENTION when a CAS loop reached `cap` retries. */
+static __device__ __forceinline__ uint32_t hr_ep_apply(unsigned long long* shadow, unsigned long long n_words,
+                                                       unsigned long long idx, uint32_t report_word, uint32_t tid,
+                                                       uint32_t op, uint32_t bc, uint32_t wc, uint32_t kernel,
+                                                       const hr_geom& g, hr_race* ring, unsigned long long ring_cap,
+                                                       unsigned long long* n_races, unsigned int* flags,
+                                                       uint32_t region, uint32_t cap)
+{
+    const uint32_t ktag = kernel & 7u;
+    const uint32_t holds = op == HR_R ? 1u : (op == HR_A ? 2u : 3u);
+    const uint32_t against = op == HR_R ? 2u : (op == HR_A ? 1u : 3u);
+    for (uint32_t b = 0; b < 2; ++b) {
+        if (((holds >> b) & 1u) == 0) continue;
+        unsigned long long* p = shadow + b * n_words + idx;
+        uint64_t o = hr_ld_relaxed(p);
+        for (uint32_t tries = 0;; ++tries) {
+            const uint64_t n = hr_ep_update(o, tid, bc, wc, ktag, g);
+            if (n == o) break;
+            const uint64_t seen = atomicCAS(p, (unsigned long long)o, (unsigned long long)n);
+            if (seen == o) break;
+            if (tries + 1 >= cap) return HR_ERR_CONTENTION;
+            o = seen;
+        }
+    }
+    asm volatile("fence.sc.gpu;" ::: "memory");
+    uint32_t prior = 0;
+    for (uint32_t b = 0; b < 2 && !prior; ++b) {
+        if (((against >> b) & 1u) == 0) continue;
+        const uint64_t s = hr_ld_relaxed(shadow + b * n_words + idx);
+        if (hr_ep_pred(s, tid, bc, wc, ktag, g)) prior = hr_ep_level(s, ktag);
+    }
+    if (!prior) return 0;
+    unsigned long long* st = shadow + 2 * n_words + idx;
+    const unsigned long long mine = ((((unsigned long long)kernel) << 16) | bc) + 1ull;
+    unsigned long long cur = hr_ld_relaxed(st);
+    for (uint32_t tries = 0; cur < mine && tries < cap; ++tries) {
+        const unsigned long long seen = atomicCAS(st, cur, mine);
+        if (seen == cur) {
+            hr_append_race(ring, ring_cap, n_races, flags, report_word, tid, kernel, bc, region, op, prior);
+            return 0;
+        }
+        cur = seen;
+    }
+    return cur < mine ? HR_ERR_CONTENTION : 0u;
+}
+
+/* ---------------------------------------------------------------------------
  * Hand instrumentation
  * ------------------------------------------------------------------------- */
 
@@ -350,6 +479,13 @@ static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long
     }
     if (!hr_fits(c.tid, c.bc, c.wc, v.geom)) {
         hr_set_error(v.error, HR_ERR_CLOCK_OVERFLOW);
+        return;
+    }
+    if (v.geom.report_mode == HR_REPORT_EVERY_EPOCH) {
+        const uint32_t st = hr_ep_apply(v.shadow, v.n_words, word, (uint32_t)abs_word, c.tid, op, c.bc, c.wc,
+                                        v.kernel, v.geom, v.ring, v.ring_cap, v.n_races, v.flags, v.region,
+                                        HR_CAS_RETRY_CAP);
+        if (st) hr_set_error(v.error, st);
         return;
     }
     const uint32_t ktag = v.kernel & 7u;

@@ -134,6 +134,8 @@ static hr_status init_impl(hr_ctx** out, const hr_region_desc* regions, uint32_t
             d.warp_size > 32 || d.reserved != 0 || d.space > HR_SPACE_SHARED)
             return HR_ERR_INVALID;
         if (d.shadow_bytes != 0 && d.shadow_bytes != 4 && d.shadow_bytes != 8) return HR_ERR_INVALID;
+        if (d.report_mode > HR_REPORT_EVERY_EPOCH || (d.report_mode == HR_REPORT_EVERY_EPOCH && d.shadow_bytes == 4))
+            return HR_ERR_INVALID;
         if (d.shadow_bytes == 4) {
             const uint32_t t = hr_desc_tid_bits(d);
             if (t < 4 || t > 22 || d.block_dim > (1u << t)) return HR_ERR_INVALID;

@@ -8,7 +8,8 @@
 
 // Geometry with exact reciprocals and, when both sizes are powers of two,
 // shifts; plus the shadow packing (8 bytes, or 4 with a tid_bits-wide tid).
-inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size, uint32_t shadow_bytes = 8, uint32_t tid_bits = 0)
+inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size, uint32_t shadow_bytes = 8, uint32_t tid_bits = 0,
+                            uint32_t report_mode = HR_REPORT_FIRST)
 {
     auto magic = [](uint32_t d) { return d <= 1 ? 0ull : (~0ull) / d + 1ull; };
     auto log2_exact = [](uint32_t d) -> uint32_t {
@@ -25,20 +26,25 @@ inline hr_geom hr_make_geom(uint32_t block_dim, uint32_t warp_size, uint32_t sha
     const uint32_t bs = log2_exact(block_dim), ws = log2_exact(warp_size);
     g.bd_shift = (bs != ~0u && ws != ~0u) ? bs : ~0u;
     g.ws_shift = (bs != ~0u && ws != ~0u) ? ws : ~0u;
-    g.shadow_bytes = shadow_bytes == 4 ? 4u : 8u;
+    g.report_mode = report_mode;
+    g.shadow_bytes = report_mode == HR_REPORT_EVERY_EPOCH ? 24u : (shadow_bytes == 4 ? 4u : 8u);
     g.tid_bits = g.shadow_bytes == 4 ? (tid_bits ? tid_bits : 16u) : 0u;
     return g;
 }
 
-// Bytes per shadow word and tid width of a region descriptor (defaults applied).
-inline uint32_t hr_desc_shadow_bytes(const hr_region_desc& d) { return d.shadow_bytes == 4 ? 4u : 8u; }
+// Bytes per shadow word and tid width of a region descriptor (defaults applied):
+// 8, 4 for the compact packing, 24 (three 8-byte arrays) in every-epoch mode.
+inline uint32_t hr_desc_shadow_bytes(const hr_region_desc& d)
+{
+    return d.report_mode == HR_REPORT_EVERY_EPOCH ? 24u : (d.shadow_bytes == 4 ? 4u : 8u);
+}
 inline uint32_t hr_desc_tid_bits(const hr_region_desc& d)
 {
     return d.shadow_bytes == 4 ? (d.tid_bits ? d.tid_bits : 16u) : 0u;
 }
 inline hr_geom hr_desc_geom(const hr_region_desc& d)
 {
-    return hr_make_geom(d.block_dim, d.warp_size, hr_desc_shadow_bytes(d), hr_desc_tid_bits(d));
+    return hr_make_geom(d.block_dim, d.warp_size, d.shadow_bytes == 4 ? 4u : 8u, hr_desc_tid_bits(d), d.report_mode);
 }
 
 // Per-region state in device memory.

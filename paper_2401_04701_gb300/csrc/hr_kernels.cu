@@ -559,6 +559,17 @@ __device__ __noinline__ Retry retry_cas(unsigned long long* shadow, unsigned wor
     return r;
 }
 
+// Every-epoch mode: one access through the per-conflict-bit summaries (cold
+// relative to the first-race path, kept out of line).
+__device__ __noinline__ unsigned every_epoch_record(unsigned long long* shadow, unsigned long long n_words,
+                                                   unsigned idx, unsigned abs_word, unsigned tid, unsigned op,
+                                                   unsigned bc, unsigned wc, unsigned kern, const hr_geom& g,
+                                                   hr_region_dev* region, unsigned cap)
+{
+    return hr_ep_apply(shadow, n_words, idx, abs_word, tid, op, bc, wc, kern, g, region->ring, region->ring_cap,
+                       &region->n_races, &region->flags, region->region, cap);
+}
+
 template <int TILE>
 __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, TileInfo* s_info, uint64_t* s_full,
                               uint64_t* s_empty)
@@ -792,6 +803,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             const unsigned bc = bcwc >> 16;
             const unsigned wc = bcwc & 0xFFFFu;
             const unsigned ktag = kern & 7u;
+            const bool every = g.report_mode == HR_REPORT_EVERY_EPOCH;  // non-absorbing reports
             unsigned err = 0;
             unsigned c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
             unsigned word[HR_RPL], grp[HR_RPL], tidv[HR_RPL], opv[HR_RPL];
@@ -831,7 +843,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 tidv[k] = v.y;
                 opv[k] = op;
                 grp[k] = 1u << lane;
-                if (AGG) {
+                if (AGG && !every) {
                     const unsigned am = __ballot_sync(0xffffffffu, a);
                     const unsigned w1 = __shfl_up_sync(0xffffffffu, v.x, 1);
                     const unsigned w2 = __shfl_up_sync(0xffffffffu, v.x, 2);
@@ -869,6 +881,26 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             if (err) hr_set_error(&region->error, err);
             __syncwarp();
 
+            if (every) {
+                if (!ready) {
+                    bool ok = true;
+                    if (lane == 0)
+                        ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
+                    ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                    __syncwarp();
+                    if (!ok) break;
+                    known = t_dep;
+                }
+#pragma unroll
+                for (int k = 0; k < HR_RPL; ++k) {
+                    if (!act[k]) continue;
+                    c_acc++;
+                    const unsigned abs_word = word[k] + (filtering ? (unsigned)filt.word_lo : 0u);
+                    const unsigned st = every_epoch_record(shadow, n_words, word[k], abs_word, tidv[k], opv[k], bc,
+                                                           wc, kern, g, region, w.cas_cap);
+                    if (st) hr_set_error(&region->error, st);
+                }
+            } else {
             // Shadow values.  When the previous stage is still running they are
             // loaded before waiting for it (the loads overlap the wait) and may be
             // stale: every CAS then goes out, so a stale value fails and is refolded
@@ -933,6 +965,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                                    kern, bc, region->region, ro, raced[k] - 1u);
                 }
             }
+            }  // first-race mode
             count(c_acc, c_cas, c_retry, c_merged);
         }
         // the warp's part of the tile is done; the CTA's last warp to finish it

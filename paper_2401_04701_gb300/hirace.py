@@ -24,6 +24,7 @@ STATUS = {0: "HR_OK", 1: "HR_ERR_INVALID", 2: "HR_ERR_OOM", 3: "HR_ERR_CUDA", 4:
           9: "HR_ERR_UNSUPPORTED", 10: "HR_ERR_CAPACITY", 11: "HR_ERR_NOT_READY"}
 STATUS_CODE = {v: k for k, v in STATUS.items()}
 FLAG_TRUNCATED = 1
+REPORT_FIRST, REPORT_EVERY_EPOCH = 0, 1
 SPACE_GLOBAL, SPACE_SHARED = 0, 1
 SYNC_KERNEL = 0
 
@@ -31,13 +32,14 @@ SYNC_KERNEL = 0
 class HrRegionDesc(ctypes.Structure):
     _fields_ = [("n_words", ctypes.c_uint64), ("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32),
                 ("space", ctypes.c_uint32), ("shadow_bytes", ctypes.c_uint8), ("tid_bits", ctypes.c_uint8),
-                ("reserved", ctypes.c_uint16), ("report_capacity", ctypes.c_uint64)]
+                ("report_mode", ctypes.c_uint8), ("reserved", ctypes.c_uint8), ("report_capacity", ctypes.c_uint64)]
 
 
 class HrGeom(ctypes.Structure):
     _fields_ = [("block_dim", ctypes.c_uint32), ("warp_size", ctypes.c_uint32), ("bd_magic", ctypes.c_uint64),
                 ("ws_magic", ctypes.c_uint64), ("bd_shift", ctypes.c_uint32), ("ws_shift", ctypes.c_uint32),
-                ("shadow_bytes", ctypes.c_uint32), ("tid_bits", ctypes.c_uint32)]
+                ("shadow_bytes", ctypes.c_uint32), ("tid_bits", ctypes.c_uint32), ("report_mode", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32)]
 
 
 class HrFilter(ctypes.Structure):
@@ -59,7 +61,7 @@ class HrView(ctypes.Structure):
                 ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32), ("filter", HrFilter)]
 
 
-assert ctypes.sizeof(HrView) == 144
+assert ctypes.sizeof(HrView) == 152
 
 
 class HiRaceError(RuntimeError):
@@ -180,8 +182,9 @@ class Checker:
 
     ``regions`` is a list of dicts with keys n_words, block_dim and optional
     warp_size (32), space (global), report_capacity (0 = the default),
-    shadow_bytes (8, or 4 for the compact packing) and tid_bits (compact
-    packing: tid width, 0 = 16).
+    shadow_bytes (8, or 4 for the compact packing), tid_bits (compact
+    packing: tid width, 0 = 16) and report_mode (REPORT_FIRST: the first racy
+    epoch of each word per kernel; REPORT_EVERY_EPOCH: every racy epoch).
     """
 
     def __init__(self, regions, report_capacity: int = 1 << 20, stream=None, buffers=None):
@@ -197,6 +200,7 @@ class Checker:
             arr[i].space = int(r.get("space", SPACE_GLOBAL))
             arr[i].shadow_bytes = int(r.get("shadow_bytes", 0))
             arr[i].tid_bits = int(r.get("tid_bits", 0))
+            arr[i].report_mode = int(r.get("report_mode", REPORT_FIRST))
             arr[i].reserved = 0
             arr[i].report_capacity = int(r.get("report_capacity", 0))
         self.regions = [dict(r) for r in regions]
@@ -210,7 +214,8 @@ class Checker:
                 raise ValueError("one buffer entry per region")
             pairs = [b if isinstance(b, (tuple, list)) else (b, None) for b in buffers]
             for i, (sh, ring) in enumerate(pairs):
-                need = int(regions[i]["n_words"]) * (4 if int(regions[i].get("shadow_bytes", 8)) == 4 else 8)
+                need = int(regions[i]["n_words"]) * (24 if int(regions[i].get("report_mode", 0)) else
+                                                     4 if int(regions[i].get("shadow_bytes", 8)) == 4 else 8)
                 if not sh.is_cuda or sh.numel() * sh.element_size() < need:
                     raise ValueError("shadow buffer %d must be a device tensor of >= %d bytes" % (i, need))
                 cap = int(regions[i].get("report_capacity", 0)) or report_capacity
