@@ -298,6 +298,9 @@ hr_status hr_destroy(hr_ctx* ctx);
  * `stream`, synchronous), keeps the fastest for this context's later checks,
  * writes it to *best and the per-variant milliseconds to ms[0..ms_cap), and
  * leaves the region reset.  Returns the region's error if the trace is bad.
+ * Regions in HR_REPORT_EVERY_EPOCH mode always use a checker of their own
+ * (variant 3's shape): the variant setting does not apply to them, and
+ * hr_autotune on such a region returns HR_ERR_INVALID.
  */
 uint32_t hr_variant_count(void);
 hr_status hr_variant_desc(uint32_t id, uint32_t* aggregate, uint32_t* records_per_lane, uint32_t* consumer_warps);

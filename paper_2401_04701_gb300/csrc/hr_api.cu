@@ -248,7 +248,8 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
     w.test_flags = ctx->test_flags;
-    const unsigned variant = aggregate ? ctx->variant : (ctx->variant | 1u);  // odd ids do not aggregate
+    unsigned variant = aggregate ? ctx->variant : (ctx->variant | 1u);  // odd ids do not aggregate
+    if (r.desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
     cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, variant, s,
                                    ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
@@ -345,7 +346,10 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
     hr_work w = ctx->batch;
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
-    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, ctx->variant, s,
+    unsigned variant = ctx->variant;
+    for (const auto& d : js)
+        if (ctx->regions[d.region].desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
+    cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, variant, s,
                                    ctx->profile ? pc.mid : nullptr);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
@@ -524,6 +528,8 @@ extern "C" hr_status hr_autotune(hr_ctx* ctx, uint32_t region, const hr_record* 
                                  hr_stream_t stream, uint32_t* best, float* ms, uint32_t ms_cap)
 {
     if (!valid_region(ctx, region) || !d_trace || n == 0 || (ms_cap > 0 && !ms)) return HR_ERR_INVALID;
+    // every-epoch regions always run their own checker; there is nothing to choose
+    if (ctx->regions[region].desc.report_mode == HR_REPORT_EVERY_EPOCH) return HR_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaEventCreate(&a);

@@ -185,7 +185,17 @@ struct hr_variant {
 };
 constexpr hr_variant HR_VARIANTS[] = {{1, 4, 8}, {0, 4, 8}, {1, 2, 8}, {0, 2, 8}, {1, 8, 4}, {0, 8, 4}};
 constexpr unsigned HR_N_VARIANTS = sizeof(HR_VARIANTS) / sizeof(HR_VARIANTS[0]);
-constexpr unsigned hr_variant_tile(unsigned v) { return HR_VARIANTS[v].consumers * 32u * HR_VARIANTS[v].rpl; }
+// Internal id of the checker that also carries the every-epoch path (shape of
+// variant 3); checks on regions in that report mode use it.
+constexpr unsigned HR_EVERY_EPOCH_VARIANT = HR_N_VARIANTS;
+constexpr unsigned hr_variant_consumers(unsigned v)
+{
+    return v == HR_EVERY_EPOCH_VARIANT ? 8u : (unsigned)HR_VARIANTS[v].consumers;
+}
+constexpr unsigned hr_variant_tile(unsigned v)
+{
+    return v == HR_EVERY_EPOCH_VARIANT ? 8u * 32u * 2u : HR_VARIANTS[v].consumers * 32u * HR_VARIANTS[v].rpl;
+}
 #ifndef HR_RING_DEPTH
 #define HR_RING_DEPTH 2
 #endif

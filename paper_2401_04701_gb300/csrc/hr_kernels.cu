@@ -651,7 +651,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
     }
 }
 
-template <bool AGG, int HR_RPL, int HR_CONSUMERS>
+template <bool AGG, int HR_RPL, int HR_CONSUMERS, bool EVERY>
 __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR_RPL, HR_CONSUMERS>::MIN_CTAS)
     hr_check_kernel(hr_region_dev* __restrict__ regions,
                                                                  hr_work w,
@@ -803,7 +803,8 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             const unsigned bc = bcwc >> 16;
             const unsigned wc = bcwc & 0xFFFFu;
             const unsigned ktag = kern & 7u;
-            const bool every = g.report_mode == HR_REPORT_EVERY_EPOCH;  // non-absorbing reports
+            // non-absorbing reports: only the EVERY instantiation carries that path
+            const bool every = EVERY && g.report_mode == HR_REPORT_EVERY_EPOCH;
             unsigned err = 0;
             unsigned c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
             unsigned word[HR_RPL], grp[HR_RPL], tidv[HR_RPL], opv[HR_RPL];
@@ -1008,34 +1009,36 @@ __global__ void hr_reconfigure_state(hr_region_dev* region, unsigned long long n
 
 __global__ void hr_set_filter_state(hr_region_dev* region, hr_filter filter) { region->filter = filter; }
 
-int g_grid[HR_N_VARIANTS] = {};
+int g_grid[HR_N_VARIANTS + 1] = {};
 
-template <bool AGG, int RPL, int CONS>
+template <bool AGG, int RPL, int CONS, bool EVERY = false>
 int grid_for()
 {
     using S = Shape<RPL, CONS>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(hr_check_kernel<AGG, RPL, CONS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::BYTES);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<AGG, RPL, CONS>, S::THREADS, S::BYTES);
+    cudaFuncSetAttribute(hr_check_kernel<AGG, RPL, CONS, EVERY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)S::BYTES);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, hr_check_kernel<AGG, RPL, CONS, EVERY>, S::THREADS,
+                                                  S::BYTES);
     if (per_sm < 1) per_sm = 1;
     return sms * per_sm;
 }
 
-template <bool AGG, int RPL, int CONS>
+template <bool AGG, int RPL, int CONS, bool EVERY = false>
 void launch_variant(int grid, hr_region_dev* d_regions, const hr_work& w, const unsigned char* d_table,
                     cudaStream_t stream)
 {
     using S = Shape<RPL, CONS>;
-    hr_check_kernel<AGG, RPL, CONS><<<grid, S::THREADS, S::BYTES, stream>>>(d_regions, w, d_table);
+    hr_check_kernel<AGG, RPL, CONS, EVERY><<<grid, S::THREADS, S::BYTES, stream>>>(d_regions, w, d_table);
 }
 
 }  // namespace
 
 int hr_check_grid_size(unsigned variant)
 {
-    if (variant >= HR_N_VARIANTS) variant = 0;
+    if (variant > HR_EVERY_EPOCH_VARIANT) variant = 0;
     int& cached = g_grid[variant];
     if (cached) return cached;
     switch (variant) {
@@ -1044,7 +1047,8 @@ int hr_check_grid_size(unsigned variant)
     case 2: cached = grid_for<true, 2, 8>(); break;
     case 3: cached = grid_for<false, 2, 8>(); break;
     case 4: cached = grid_for<true, 8, 4>(); break;
-    default: cached = grid_for<false, 8, 4>(); break;
+    case 5: cached = grid_for<false, 8, 4>(); break;
+    default: cached = grid_for<false, 2, 8, true>(); break;
     }
     return cached;
 }
@@ -1073,10 +1077,10 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
                            const unsigned char* d_table, unsigned variant, cudaStream_t stream,
                            cudaEvent_t before_check)
 {
-    if (variant >= HR_N_VARIANTS) return cudaErrorInvalidValue;
+    if (variant > HR_EVERY_EPOCH_VARIANT) return cudaErrorInvalidValue;
     hr_work w = w_in;
     w.tile = hr_variant_tile(variant);
-    w.consumers = (unsigned)HR_VARIANTS[variant].consumers;
+    w.consumers = hr_variant_consumers(variant);
     const int grid = hr_check_grid_size(variant);
     if (n_jobs == 0 || n_jobs > HR_MAX_BATCH || n_jobs > w.max_jobs) return cudaErrorInvalidValue;
     const unsigned total_int = jobs[n_jobs - 1].int_begin + jobs[n_jobs - 1].n_int;
@@ -1099,7 +1103,8 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
     case 2: launch_variant<true, 2, 8>(grid, d_regions, w, d_table, stream); break;
     case 3: launch_variant<false, 2, 8>(grid, d_regions, w, d_table, stream); break;
     case 4: launch_variant<true, 8, 4>(grid, d_regions, w, d_table, stream); break;
-    default: launch_variant<false, 8, 4>(grid, d_regions, w, d_table, stream); break;
+    case 5: launch_variant<false, 8, 4>(grid, d_regions, w, d_table, stream); break;
+    default: launch_variant<false, 2, 8, true>(grid, d_regions, w, d_table, stream); break;
     }
     return cudaGetLastError();
 }
