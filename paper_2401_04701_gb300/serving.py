@@ -34,6 +34,7 @@ from . import hirace
 from . import tracegen as tg
 
 RING = 1 << 17  # race records kept per request
+CANCELLED = -1  # Result.status of a request cancelled before it finished
 
 
 @dataclass
@@ -44,6 +45,7 @@ class Request:
     source: str = ""                    # trace pool entry, or kernel name
     length: int = 0                     # records (trace) or threads (kernel)
     seed: int = 0
+    timeout: float = 0.0                # cancel if not done this long after arrival (0: never)
 
 
 @dataclass
@@ -122,6 +124,7 @@ class Server:
         self.pool = pool
         self.device = device
         self.n_slots = n_slots
+        self.slot_words = slot_words
         self.budget = budget_bytes
         self.chunk = chunk_records          # smallest chunk a job gets per iteration
         self.iteration_records = iteration_records  # records shared by the active jobs per iteration
@@ -151,8 +154,53 @@ class Server:
             words = kernel_words(req.source, req.length)
         return words * 8 + RING * 16
 
+    def _words(self, req):
+        if req.kind == "trace":
+            return self.pool.entries[req.source]["n_words"]
+        return kernel_words(req.source, req.length)
+
+    def _finish_unserved(self, req, status):
+        t = self._now() if self.t0 is not None else 0.0
+        self.results[req.rid] = Result(req.rid, req.kind, status, np.zeros(0, hirace.RACE_DTYPE), 0, 0,
+                                       req.arrival, t, t)
+
     def submit(self, req: Request):
+        """Queue a request.  One that can never be admitted (its shadow does not
+        fit a slot or the whole budget) is answered at once with HR_ERR_OOM
+        instead of blocking the queue behind it."""
+        if self._words(req) > self.slot_words or self._footprint(req) > self.budget:
+            self._finish_unserved(req, hirace.STATUS_CODE["HR_ERR_OOM"])
+            return
         self.queue.append(req)
+
+    def _expire(self, now):
+        """Cancel queued or running requests whose timeout has passed."""
+        late = [r.rid for r in self.queue if r.timeout and now > r.arrival + r.timeout]
+        late += [j["req"].rid for j in self.active.values()
+                 if j["req"].timeout and now > j["req"].arrival + j["req"].timeout]
+        for rid in late:
+            self.cancel(rid)
+
+    def cancel(self, rid: int) -> bool:
+        """Cancel a request: dropped if still queued; a trace job being checked
+        gets no further chunks and its slot is freed once its launched chunks
+        finish.  Its result has status CANCELLED.  False if it already finished."""
+        for req in self.queue:
+            if req.rid == rid:
+                self.queue.remove(req)
+                self._finish_unserved(req, CANCELLED)
+                return True
+        for slot, job in list(self.active.items()):
+            if job["req"].rid == rid:
+                del self.active[slot]
+                job["cancelled"] = True
+                # the slot comes back once the chunks already queued on the GPU are done
+                import torch
+                ev = torch.cuda.Event()
+                ev.record(self.stream)
+                self.inflight.append((ev, [(slot, job)]))
+                return True
+        return False
 
     def _admit(self):
         import torch
@@ -226,8 +274,11 @@ class Server:
             for slot, job in finished:
                 races, status, n_total, _ = self.ck.report(slot)
                 req = job["req"]
+                acc = job["accesses"]
+                if job.get("cancelled"):
+                    status, races, n_total, acc = CANCELLED, races[:0], 0, 0
                 self.results[req.rid] = Result(req.rid, req.kind, status, races.copy(), n_total,
-                                               job["accesses"], req.arrival, job["admitted"], t)
+                                               acc, req.arrival, job["admitted"], t)
                 self.free.append(slot)
                 self.used -= job["need"]
 
@@ -263,6 +314,7 @@ class Server:
                 break
             while pending and pending[0].arrival <= now:
                 self.submit(pending.popleft())
+            self._expire(now)
             self._admit()
             launched = self._launch_iteration()
             self._poll()

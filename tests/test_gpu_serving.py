@@ -48,3 +48,40 @@ def test_alone_equals_mix(oracle_mod, env):
             prefix = e["host"][: min(r.length, e["n"])]
             want = oracle_mod.race_keys(oracle_mod.bruteforce(prefix, e["block_dim"]))
             assert m.keys() == want, r
+
+
+def test_failures_stay_with_their_request(oracle_mod, env):
+    """Host-side fault injection in a served mix: malformed traces end with their
+    own error status, a request too large for any slot is refused at once, a
+    request that overruns its timeout is cancelled and its slot reused, and every
+    other request still gets the oracle's races."""
+    import torch
+    from paper_2401_04701_gb300 import hirace, tracegen as tg
+    serving, pool = env
+    dev = torch.device("cuda", 0)
+    tr, info = tg.gen_global_mix(tg.seed_for(5, 9), inject=True, n_blocks=8)
+    unsorted = tr.copy()
+    unsorted[[100, len(tr) - 100]] = unsorted[[len(tr) - 100, 100]]   # two records out of wave order
+    pool._add("unsorted", unsorted, info, dev)
+    pool._add("out_of_range", tr, dict(info, n_words=1 << 16), dev)  # words beyond the region
+    pool._add("huge", tr, dict(info, n_words=1 << 30), dev)          # no slot holds 2^30 words
+    long_tr, long_info = tg.gen_powerlaw_push(tg.seed_for(5, 10), log2_vertices=18, sweeps=4)
+    pool._add("long", long_tr, long_info, dev)
+    R = serving.Request
+    reqs = [R(0, 0.000, "trace", "global", 400_000, 1), R(1, 0.001, "trace", "unsorted", len(tr), 2),
+            R(2, 0.002, "trace", "tree", 300_000, 3), R(3, 0.003, "trace", "out_of_range", len(tr), 4),
+            R(4, 0.004, "trace", "huge", 1000, 5), R(5, 0.005, "trace", "long", len(long_tr), 6, timeout=1e-4),
+            R(6, 0.006, "kernel", "stencil", 1 << 16, 7), R(7, 0.007, "trace", "graph", 200_000, 8)]
+    srv = serving.Server(pool, dev, n_slots=3, slot_words=1 << 22, chunk_records=1 << 16,
+                         iteration_records=1 << 17)
+    res = srv.run(reqs)
+    name = lambda rid: hirace.STATUS.get(res[rid].status, res[rid].status)
+    assert name(1) == "HR_ERR_ORDER" and name(3) == "HR_ERR_RANGE" and name(4) == "HR_ERR_OOM"
+    assert res[5].status == serving.CANCELLED
+    for rid in (0, 2, 7):
+        r = reqs[rid]
+        e = pool.entries[r.source]
+        want = oracle_mod.race_keys(oracle_mod.bruteforce(e["host"][: min(r.length, e["n"])], e["block_dim"]))
+        assert res[rid].status == hirace.HR_OK and res[rid].keys() == want, r
+    assert res[6].status == hirace.HR_OK
+    assert sorted(srv.free) == [0, 1, 2] and srv.used == 0   # every slot came back
