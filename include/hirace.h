@@ -173,6 +173,20 @@ hr_status hr_check_trace(hr_ctx* ctx, uint32_t region, const hr_record* d_trace,
                          hr_stream_t stream);
 
 /*
+ * hr_check_trace_host - hr_check_trace over a trace in HOST memory: the trace
+ * is copied in chunks of chunk_records records (0: 2^24, i.e. 256 MB) through
+ * two device staging buffers owned by the context, each chunk's copy (on a
+ * copy stream of the context) overlapping the check of the chunk before it on
+ * `stream`.  Chunks may cut waves (the shadow stays resident between them).
+ * Asynchronous: h_trace must stay valid, and unchanged, until `stream` has
+ * passed this call; page-locked memory lets the copies overlap the checks.
+ * Growing the staging buffers synchronises the device once.  Not for use
+ * inside stream capture.  Errors: those of hr_check_trace, HR_ERR_OOM.
+ */
+hr_status hr_check_trace_host(hr_ctx* ctx, uint32_t region, const hr_record* h_trace, uint64_t n,
+                              uint64_t chunk_records, hr_stream_t stream);
+
+/*
  * hr_check_trace_kbase - hr_check_trace with `kernel_base` (0..65535) added to
  * every record's kernel ordinal: one recorded trace can be checked again as a
  * later launch without clearing the region (kernel end orders everything,

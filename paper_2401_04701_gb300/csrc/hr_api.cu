@@ -76,6 +76,13 @@ struct hr_ctx {
     unsigned variant = 0;              // kernel variant of later checks (hr_set_variant / hr_autotune)
     cudaStream_t copies = nullptr;     // non-blocking stream for report copies (never waits on user streams)
     void* batch_mem = nullptr;         // scratch of hr_check_batch (allocated on first use)
+    // hr_check_trace_host: two device staging buffers, a copy stream, and events
+    // ordering each buffer's copy before its check and its check before its next copy
+    hr_record* stage_buf[2] = {nullptr, nullptr};
+    uint64_t stage_cap = 0;            // records per staging buffer
+    cudaStream_t h2d = nullptr;
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    cudaEvent_t used[2] = {nullptr, nullptr};
     hr_work batch{};
     unsigned batch_jobs = 0;
     unsigned long long batch_waves = 0;
@@ -113,6 +120,12 @@ static void free_ctx(hr_ctx* c)
             cudaEventDestroy(p.end);
         }
     if (c->copies) cudaStreamDestroy(c->copies);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->stage_buf[b]);
+        if (c->copied[b]) cudaEventDestroy(c->copied[b]);
+        if (c->used[b]) cudaEventDestroy(c->used[b]);
+    }
+    if (c->h2d) cudaStreamDestroy(c->h2d);
     cudaFree(c->batch_mem);
     cudaFree(c->d_regions);
     cudaFree(c->d_table);
@@ -265,6 +278,52 @@ extern "C" hr_status hr_check_trace(hr_ctx* ctx, uint32_t region, const hr_recor
                                     hr_stream_t stream)
 {
     return check_common(ctx, region, d_trace, n, 0, stream, true);
+}
+
+extern "C" hr_status hr_check_trace_host(hr_ctx* ctx, uint32_t region, const hr_record* h_trace, uint64_t n,
+                                         uint64_t chunk_records, hr_stream_t stream)
+{
+    if (!valid_region(ctx, region) || (n > 0 && !h_trace) || n >= (1ull << 40)) return HR_ERR_INVALID;
+    if (n == 0) return HR_OK;
+    if (chunk_records == 0) chunk_records = 1ull << 24;  // 256 MB per staging buffer
+    if (chunk_records > n) chunk_records = n;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    if (!ctx->h2d) e = cudaStreamCreateWithFlags(&ctx->h2d, cudaStreamNonBlocking);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+        if (!ctx->copied[b]) e = cudaEventCreateWithFlags(&ctx->copied[b], cudaEventDisableTiming);
+        if (e == cudaSuccess && !ctx->used[b]) e = cudaEventCreateWithFlags(&ctx->used[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && chunk_records > ctx->stage_cap) {
+        // earlier calls may still read the old buffers
+        e = cudaDeviceSynchronize();
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            cudaFree(ctx->stage_buf[b]);
+            ctx->stage_buf[b] = nullptr;
+            e = cudaMalloc(&ctx->stage_buf[b], chunk_records * sizeof(hr_record));
+        }
+        ctx->stage_cap = e == cudaSuccess ? chunk_records : 0;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    hr_status st = HR_OK;
+    uint64_t i = 0;
+    for (uint64_t off = 0; off < n && st == HR_OK; off += chunk_records, ++i) {
+        const int b = (int)(i & 1);
+        const uint64_t m = n - off < chunk_records ? n - off : chunk_records;
+        // the copy into buffer b waits for the check that last read it, the check for the copy
+        e = cudaStreamWaitEvent(ctx->h2d, ctx->used[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ctx->stage_buf[b], h_trace + off, m * sizeof(hr_record), cudaMemcpyHostToDevice,
+                                ctx->h2d);
+        if (e == cudaSuccess) e = cudaEventRecord(ctx->copied[b], ctx->h2d);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ctx->copied[b], 0);
+        if (e != cudaSuccess) return cuda_status(e);
+        st = check_common(ctx, region, ctx->stage_buf[b], m, 0, stream, true);
+        e = cudaEventRecord(ctx->used[b], s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return st;
 }
 
 extern "C" hr_status hr_check_trace_kbase(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,

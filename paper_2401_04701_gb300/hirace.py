@@ -88,6 +88,7 @@ def load_library():
     lib.hr_init_with_buffers.argtypes = [ctypes.POINTER(P), ctypes.POINTER(HrRegionDesc), u32, u64,
                                          ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.hr_set_filter.argtypes = [P, u32, ctypes.POINTER(HrFilter), P]
+    lib.hr_check_trace_host.argtypes = [P, u32, P, u64, u64, P]
     lib.hr_check_trace.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_plain.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_kbase.argtypes = [P, u32, P, u64, u32, P]
@@ -246,6 +247,20 @@ class Checker:
             fn = self._lib.hr_check_trace if aggregate else self._lib.hr_check_trace_plain
             rc = fn(self._ctx, region, ptr, n, st)
         self._check(rc, "hr_check_trace")
+
+    def check_trace_host(self, region: int, trace, chunk_records: int = 0, stream=None):
+        """Queue a check of a trace in host memory (a CPU tensor or a numpy array of
+        16-byte records; page-locked for overlap), copied in chunks that overlap the
+        checks.  Keep `trace` alive until the stream has passed this call."""
+        import torch
+        if isinstance(trace, np.ndarray):
+            ptr, n = trace.ctypes.data, trace.nbytes // 16
+        else:
+            if trace.is_cuda:
+                raise ValueError("check_trace_host takes host memory; use check_trace for device traces")
+            ptr, n = trace.data_ptr(), trace.numel() * trace.element_size() // 16
+        self._check(self._lib.hr_check_trace_host(self._ctx, region, ctypes.c_void_p(ptr), n, chunk_records,
+                                                  _stream_handle(stream)), "hr_check_trace_host")
 
     def check_batch(self, jobs, stream=None):
         """Queue one batched check: ``jobs`` is a list of (region, device trace tensor)

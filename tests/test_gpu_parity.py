@@ -328,3 +328,19 @@ def test_autotune_keeps_the_fastest(oracle_mod, hr):
         ck.check_trace(0, d)
         races, status, _, _ = ck.report(0)
     assert status == hr.HR_OK and hr.race_keys(races) == want
+
+
+@pytest.mark.parametrize("chunk", [0, 4096, 100_003])
+def test_check_from_host_memory(oracle_mod, hr, chunk):
+    """hr_check_trace_host: chunks copied through two staging buffers while the
+    previous chunk is checked give the oracle's races, pinned or pageable."""
+    import torch
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 11), inject=True, n_blocks=8)
+    want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, info["block_dim"]))
+    pinned = torch.from_numpy(tr.view(np.uint8)).pin_memory()
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=256)], report_capacity=1 << 20) as ck:
+        for host in (pinned, np.ascontiguousarray(tr)):
+            ck.reset(0)
+            ck.check_trace_host(0, host, chunk_records=chunk)
+            races, status, n_total, _ = ck.report(0)
+            assert status == hr.HR_OK and hr.race_keys(races) == want and n_total == len(want)
