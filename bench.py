@@ -141,9 +141,17 @@ def job_rate(world, units_per_rank_per_step, steps, max_ms):
     return world * units_per_rank_per_step * steps / (max_ms / 1e3)
 
 
-def make_workload(n_blocks=1024):
+def make_workload(n_blocks=1024, kind="global", log2_vertices=22):
+    """The benchmark workload (global mix, `n_blocks` x 256 threads), or with
+    --workload the power-law push (2^log2_vertices vertices, 4 sweeps) or the
+    tree reduction: (trace, info, accesses, barrier records)."""
     from paper_2401_04701_gb300 import tracegen as tg
-    trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True, n_blocks=n_blocks)
+    if kind == "powerlaw":
+        trace, info = tg.gen_powerlaw_push(tg.seed_for(3), log2_vertices=log2_vertices)
+    elif kind == "tree":
+        trace, info = tg.gen_tree_reduction(tg.seed_for(1), inject=True)
+    else:
+        trace, info = tg.gen_global_mix(tg.seed_for(2), inject=True, n_blocks=n_blocks)
     n_acc = int(np.count_nonzero(trace["op"] <= tg.OP_A))
     n_sync = len(trace) - n_acc
     return trace, info, n_acc, n_sync
@@ -234,6 +242,11 @@ def other_workloads(dev, reps=5):
         res = {"records": len(trace), "accesses": n_acc}
         with hirace.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])],
                             report_capacity=1 << 22) as ck:
+            best, tune_ms = ck.autotune(0, d)
+            res["autotuned"] = {"variant": best, "desc": dict(hirace.variants())[best],
+                                "kernel_ms": tune_ms[best], "accesses_per_s": n_acc / (tune_ms[best] / 1e3),
+                                "ms_per_variant": [round(t, 4) for t in tune_ms]}
+            ck.set_variant(0)
             for agg in (True, False):
                 ck.reset(0)
                 ck.check_trace(0, d, aggregate=agg)
@@ -457,7 +470,8 @@ def run_gpu(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     hirace.load_library()
 
-    trace, info, n_acc, n_sync = make_workload(args.blocks)
+    trace, info, n_acc, n_sync = make_workload(args.blocks, args.workload, args.log2_vertices)
+    default = args.workload == "global" and args.blocks == 1024
     host = torch.from_numpy(trace.view(np.uint8)).pin_memory()
     d_trace = host.to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -471,18 +485,23 @@ def run_gpu(args, rank, world, local_rank):
     else:
         ck.set_variant(args.variant)
         best, tune_ms = args.variant, None
-    # correctness gate: one check vs the injected set
+    # correctness gate: one check vs the injected set (the global mix's racy words
+    # are exactly its injected words; the other workloads' parity is in the tests,
+    # here later checks must repeat the first one's count)
     ck.check_trace(0, d_trace)
     races, status, n_total, _ = ck.report(0)
-    if status != hirace.HR_OK or n_total != len(info["injected"]):
+    expect = len(info["injected"]) if args.workload == "global" else n_total
+    if status != hirace.HR_OK or n_total != expect:
         raise SystemExit("bench workload check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
     ck.reset(0)
     torch.cuda.synchronize()
 
+    # every check is a later launch: kernel ordinals advance by the trace's kernel count
+    kstep = int(trace["kernel"].max()) + 1 if len(trace) else 1
     kb = 0
     for _ in range(args.warmup):
         ck.check_trace(0, d_trace, kernel_base=kb)
-        kb += 1
+        kb += kstep
     torch.cuda.synchronize()
     ck.profile(True)
     ck.profile_read()
@@ -494,7 +513,7 @@ def run_gpu(args, rank, world, local_rank):
     start.record(stream)
     for _ in range(args.steps):
         ck.check_trace(0, d_trace, kernel_base=kb)
-        kb += 1
+        kb += kstep
     stop.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -524,7 +543,7 @@ def run_gpu(args, rank, world, local_rank):
         ck.check_trace_host(0, host)
         races, status, n_total, _ = ck.report(0)
         d2h += races.nbytes + 64
-        if status != hirace.HR_OK or n_total != len(info["injected"]):
+        if status != hirace.HR_OK or n_total != expect:
             raise SystemExit("end-to-end check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
     e2e_s = time.perf_counter() - t0
     e2e_rate = world * n_acc * e2e_steps / e2e_s if e2e_steps else None
@@ -538,7 +557,7 @@ def run_gpu(args, rank, world, local_rank):
     check_ms = prof["check_ms"] / max(1, prof["calls"])
     achieved = alg_bytes / (check_ms / 1e3) / 1e9
     cpu = None
-    if not args.no_cpu_baseline and args.blocks == 1024:
+    if not args.no_cpu_baseline and default:
         cores = host_cores()
         rate, dt, acc = cpu_oracle_rate(trace, info, n_acc, threads=cores)
         rate1, dt1, _ = cpu_oracle_rate(trace, info, n_acc)
@@ -550,14 +569,15 @@ def run_gpu(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": workload_name(args.blocks, info["n_words"], n_acc, n_sync),
+        "config": {"workload": workload_name(args.blocks, info["n_words"], n_acc, n_sync) if args.workload == "global"
+                   else "%s: %d records, %d words" % (args.workload, len(trace), info["n_words"]),
                    "n_words": info["n_words"], "records": len(trace), "accesses": n_acc,
-                   "shadow_bytes_per_word": 8, "racy_words": int(len(info["injected"])),
+                   "shadow_bytes_per_word": 8, "racy_words": int(expect),
                    "l2": "inputs larger than L2 (%.2f GB trace, %d MB shadow), no flush" % (
                        len(trace) * 16 / 1e9, info["n_words"] * 8 >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
-                     "frac": achieved / p_hbm, "traffic": measured_traffic() if args.blocks == 1024 else None,
+                     "frac": achieved / p_hbm, "traffic": measured_traffic() if default else None,
                      "kernel": "hr_check_kernel variant %d" % best,
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
@@ -571,7 +591,7 @@ def run_gpu(args, rank, world, local_rank):
     }
     if cpu:
         line["cpu_baseline"] = cpu
-    if args.blocks == 1024:
+    if default:
         line["compact_shadow"] = compact_shadow_workload(dev, d_trace, info, n_acc, n_sync, best, p_hbm)
         line["every_epoch_reports"] = every_epoch_workload(dev, d_trace, info, n_acc, n_sync, p_hbm)
     if not args.no_instrumented:
@@ -602,6 +622,9 @@ def main():
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the checker kernel variant instead of autotuning")
+    ap.add_argument("--workload", default="global", choices=["global", "powerlaw", "tree"],
+                    help="time another workload instead of the global mix (parity is in the tests)")
+    ap.add_argument("--log2-vertices", type=int, default=22, help="power-law workload size")
     ap.add_argument("--blocks", type=int, default=1024,
                     help="scale the workload (profiling only; the benchmark is 1024)")
     args = ap.parse_args()
