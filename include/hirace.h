@@ -2,9 +2,10 @@
  * hirace.h - C-ABI of the GB300 race checker (HiRace, arXiv 2401.04701).
  *
  * The checker folds the access history of every monitored word into a
- * constant-size 8-byte shadow value with a parallel finite-state machine
- * (Sec. III; Algorithm 1 "UpdateShadow"; 8 bytes per word by default,
- * Sec. IV-B) and reports the words on which two accesses race (Sec. II-A:
+ * constant-size shadow value with a parallel finite-state machine (Sec. III;
+ * Algorithm 1 "UpdateShadow"; 8 bytes per word by default, 4 with the compact
+ * packing, 24 in every-epoch report mode; Sec. IV-B) and reports the words on
+ * which two accesses race (Sec. II-A:
  * different threads, at least one write, not ordered by happens-before;
  * Sec. II-B: __syncthreads orders a block, __syncwarp a warp, nothing orders
  * two blocks of one kernel, kernel end orders everything).
@@ -43,9 +44,11 @@ typedef enum hr_status {
     HR_ERR_NOT_READY = 11      /* the region has work in flight on another stream */
 } hr_status;
 
+/* report modes of a region (hr_region_desc.report_mode) */
+#define HR_REPORT_FIRST 0u       /* the first racy epoch of each word per kernel (RACE absorbing) */
+#define HR_REPORT_EVERY_EPOCH 1u /* every racy (word, kernel, epoch) */
+
 /* hr_report flag bits */
-#define HR_REPORT_FIRST 0u
-#define HR_REPORT_EVERY_EPOCH 1u
 #define HR_FLAG_TRUNCATED 1u /* more races than the report ring holds; n_total stays exact */
 
 /* memory space of a region (informational: the shadow always lives in HBM) */
@@ -93,7 +96,9 @@ typedef struct hr_record {
  * was completed by an access of thread `tid` doing `op` in block epoch
  * `epoch` (its bc).  `prior` is the FSM state the word held just before
  * (hr_fsm_state_name).  Races are reported once per (word, kernel): the
- * paper reports races per distinct address (Sec. V-B).
+ * paper reports races per distinct address (Sec. V-B).  In every-epoch mode
+ * a report is made once per (word, kernel, epoch) and `prior` is the scope
+ * level (1 thread .. 4 grid) of the accesses the reporting one conflicts with.
  */
 typedef struct hr_race {
     uint32_t word;
