@@ -375,8 +375,18 @@ def batch_workload(dev, reps=3):
 
         per_trace_ms = timed(lambda: [ck.check_trace(i, t) for i, t in enumerate(d)])
         races_single = sum(ck.report(i)[2] for i in range(len(d)))
+        # per-trace completion times: one launch per trace (events after each launch)
+        reset_all()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(d) + 1)]
+        evs[0].record(stream)
+        for i, t in enumerate(d):
+            ck.check_trace(i, t)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        done_single = np.array([evs[0].elapsed_time(e) for e in evs[1:]])
         batch_ms = timed(lambda: ck.check_batch(list(enumerate(d))))
         races_batch = sum(ck.report(i)[2] for i in range(len(d)))
+        done_batch = ck.batch_job_times(len(d)) / 1e6   # the last timed batch, device clock
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream(dev)
         reset_all()
@@ -392,6 +402,9 @@ def batch_workload(dev, reps=3):
                      ("batched_graph_replay", graph_ms)):
         out[name] = {"ms": ms, "accesses_per_s": n_acc / (ms / 1e3)}
     out["races"] = {"per_trace": races_single, "batched": races_batch, "graph": races_graph}
+    for name, done in (("one_launch_per_trace", done_single), ("batched_launch", done_batch)):
+        out[name]["trace_completion_ms"] = {"p50": float(np.percentile(done, 50)),
+                                            "p99": float(np.percentile(done, 99)), "max": float(done.max())}
     return out
 
 

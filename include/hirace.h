@@ -239,6 +239,16 @@ hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_jobs, hr_st
 hr_status hr_batch_reserve(hr_ctx* ctx, uint32_t max_jobs, uint64_t max_waves);
 
 /*
+ * hr_batch_job_times - completion time of each job of the last hr_check_batch,
+ * in nanoseconds after the batch's first kernel started (device clock): the
+ * moment the tile that finished the job's last wave was done.  ns_out[i] is
+ * for jobs[i] of that call (0 for an empty trace or a job that failed before
+ * running).  Synchronises the device.  HR_ERR_INVALID if n exceeds that call's
+ * job count.
+ */
+hr_status hr_batch_job_times(hr_ctx* ctx, uint64_t* ns_out, uint32_t n);
+
+/*
  * hr_sync - kernel end for a region (Sec. II-B: the end of a kernel orders
  * every access of that kernel before every access of the next one).  Only
  * HR_SYNC_KERNEL exists: block and warp barriers arrive as trace records or

@@ -85,6 +85,7 @@ struct hr_ctx {
     cudaEvent_t used[2] = {nullptr, nullptr};
     hr_work batch{};
     unsigned batch_jobs = 0;
+    std::vector<int> batch_map;        // last hr_check_batch: caller's job -> device job (-1: empty trace)
     unsigned long long batch_waves = 0;
     std::vector<ProfiledCall> calls;   // profiled calls not read yet
     std::vector<ProfiledCall> spare;   // event triples to reuse
@@ -338,6 +339,25 @@ extern "C" hr_status hr_check_trace_plain(hr_ctx* ctx, uint32_t region, const hr
     return check_common(ctx, region, d_trace, n, 0, stream, false);
 }
 
+extern "C" hr_status hr_batch_job_times(hr_ctx* ctx, uint64_t* ns_out, uint32_t n)
+{
+    if (!ctx || (n > 0 && !ns_out) || n > ctx->batch_map.size()) return HR_ERR_INVALID;
+    if (n == 0) return HR_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    std::vector<hr_jobd> jobs(ctx->batch_jobs);
+    hr_ctl ctl{};
+    if (e == cudaSuccess && ctx->batch_mem)
+        e = cudaMemcpy(jobs.data(), ctx->batch.jobs, jobs.size() * sizeof(hr_jobd), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && ctx->batch_mem) e = cudaMemcpy(&ctl, ctx->batch.ctl, sizeof ctl, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (uint32_t i = 0; i < n; ++i) {
+        const int d = ctx->batch_map[i];
+        const uint64_t t = d >= 0 && (size_t)d < jobs.size() ? jobs[d].done_ns : 0;
+        ns_out[i] = t > ctl.t0_ns ? t - ctl.t0_ns : 0;
+    }
+    return HR_OK;
+}
+
 extern "C" hr_status hr_batch_reserve(hr_ctx* ctx, uint32_t max_jobs, uint64_t max_waves)
 {
     if (!ctx || max_jobs == 0 || max_jobs > HR_MAX_BATCH || max_waves == 0 || max_waves > (1ull << 24))
@@ -367,6 +387,7 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
 {
     if (!ctx || (n_jobs > 0 && !jobs)) return HR_ERR_INVALID;
     std::vector<hr_jobd> js;
+    std::vector<int> map(n_jobs, -1);
     std::vector<char> seen(ctx->regions.size(), 0);
     for (uint32_t i = 0; i < n_jobs; ++i) {
         const hr_job& j = jobs[i];
@@ -380,8 +401,10 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
         d.trace = j.trace;
         d.n = j.n;
         d.region = j.region;
+        map[i] = (int)js.size();
         js.push_back(d);
     }
+    ctx->batch_map = map;
     if (js.empty()) return HR_OK;
     if (js.size() > HR_MAX_BATCH) return HR_ERR_INVALID;
     if (!ctx->batch_mem || ctx->batch_jobs < js.size()) {

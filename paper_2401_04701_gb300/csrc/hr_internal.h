@@ -84,6 +84,7 @@ struct hr_jobd {
     unsigned n_int;
     unsigned wave_begin;          // first global wave index (written on the device)
     unsigned n_waves;             // waves of this job (written on the device)
+    unsigned long long done_ns;   // device clock when the job's last stage completed (0: no stages)
 };
 
 // Work stages: per wave an optional shadow clear (when the kernel-tag group
@@ -100,7 +101,7 @@ struct hr_stage {
     unsigned dep;
     unsigned dep_need;
     unsigned job;
-    unsigned pad;
+    unsigned last;        // 1: the job's last stage (its completion time is recorded)
 };
 
 struct hr_ctl {
@@ -112,6 +113,7 @@ struct hr_ctl {
     unsigned n_jobs;
     unsigned n_intervals;
     unsigned pad;
+    unsigned long long t0_ns;  // device clock when the check's first kernel started
 };
 
 // Scratch of one check (device memory): job table, pre-pass counts, wave

@@ -78,8 +78,15 @@ __global__ void hr_scan_intervals(const JobParams<CAP> P, unsigned total_int, hr
     const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned n_warps = (gridDim.x * blockDim.x) >> 5;
     if (blockIdx.x == 0) {
-        for (unsigned j = threadIdx.x; j < P.n; j += blockDim.x) w.jobs[j] = P.job[j];
-        if (threadIdx.x == 0) w.ctl->n_jobs = P.n;
+        for (unsigned j = threadIdx.x; j < P.n; j += blockDim.x) {
+            hr_jobd jb = P.job[j];
+            jb.done_ns = 0;
+            w.jobs[j] = jb;
+        }
+        if (threadIdx.x == 0) {
+            w.ctl->n_jobs = P.n;
+            w.ctl->t0_ns = globaltimer();
+        }
     }
     for (unsigned i = warp; i < total_int; i += n_warps) {
         const unsigned j = job_of_interval(P, i);
@@ -271,6 +278,7 @@ __device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
     // so its bounded wait must run out and report HR_ERR_TIMEOUT
     if (threadIdx.x == 0 && (w.test_flags & HR_TEST_HOLD_STAGE) && n_st > 1) w.stages[1].dep_need += 1;
     if (threadIdx.x == 0) {
+        if (n_st > 0) w.stages[n_st - 1].last = 1u;
         w.stages[n_st] = hr_stage{(unsigned)tot, 0u, HR_STAGE_RECORDS, 0u, HR_NO_DEP, 0u, 0u, 0u};
         if (nw > 0 && w.wave_key[jb.wave_begin] < rg.last_key) hr_set_error(&rg.error, HR_ERR_ORDER);
         w.ctl->n_stages = n_st;
@@ -336,6 +344,7 @@ __device__ void stages_many_jobs(hr_work& w, hr_region_dev* regions)
         rg->last_key = w.wave_key[jb.wave_begin + nw - 1];
         rg->used = 1;
     }
+    if (j < n_jobs && last != HR_NO_DEP) w.stages[last].last = 1u;
     if (threadIdx.x == 0) {
         w.stages[base_s] = hr_stage{base_i, 0u, HR_STAGE_RECORDS, 0u, HR_NO_DEP, 0u, 0u, 0u};
         w.ctl->n_stages = base_s;
@@ -368,7 +377,9 @@ struct TileInfo {
     unsigned long long kb;           // the job's kernel base (shifted), to rebase record keys
     unsigned stage, type, item, valid;
     unsigned skip, dep, dep_need, region;
-    unsigned ready, pad[3];           // ready: the producer saw the dependency complete
+    unsigned ready;                   // the producer saw the dependency complete
+    unsigned last;                    // the stage is its job's last (its completion is timed)
+    unsigned pad[2];
 };
 
 struct Acc {
@@ -442,6 +453,13 @@ __device__ __forceinline__ unsigned smem_add_acq_rel(unsigned* p, unsigned v)
 {
     unsigned old;
     asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(smem_u32(p)), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned atom_add_release(unsigned* p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.release.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
     return old;
 }
 
@@ -576,7 +594,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
 {
     const uint64_t pol = policy_evict_first();
     const unsigned total = w.ctl->total_items;
-    unsigned s = 0, s_begin = 0, s_end = 0, type = 0, dep = HR_NO_DEP, dep_need = 0, region = 0;
+    unsigned s = 0, s_begin = 0, s_end = 0, type = 0, dep = HR_NO_DEP, dep_need = 0, region = 0, last = 0;
     unsigned long long w_start = 0, w_end = 0, key = 0, kb = 0;
     const hr_record* trace = nullptr;
     bool have = false, skip = false;
@@ -609,6 +627,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
             type = st.type;
             dep = st.dep;
             dep_need = st.dep_need;
+            last = st.last;
             const hr_jobd jb = w.jobs[st.job];
             region = jb.region;
             trace = jb.trace;
@@ -628,6 +647,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
         info.item = t - s_begin;
         info.dep = dep;
         info.dep_need = dep_need;
+        info.last = last;
         // one look at the dependency here spares every consumer warp its own poll
         info.ready = dep == HR_NO_DEP || dep == known;
         if (!info.ready && ld_acquire_u32(&w.stages[dep].done) >= dep_need) {
@@ -739,7 +759,8 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         // take what the tile needs out of the slot, then release it
         const TileInfo& ti = s_info[b];
         if (!ti.valid) break;
-        const unsigned t_type = ti.type, t_skip = ti.skip, t_stage = ti.stage, t_dep = ti.dep;
+        const unsigned t_type = ti.type, t_skip = ti.skip, t_dep = ti.dep;
+        const unsigned t_stage = ti.stage | (ti.last << 31);  // bit 31: the job's last stage
         const unsigned t_need = ti.dep_need, t_item = ti.item, t_region = ti.region, t_ready = ti.ready;
         const unsigned t_n = (unsigned)(ti.re - ti.rb);  // records in this tile (<= HR_TILE)
         const unsigned kern = (unsigned)(ti.key >> 32);  // wave key: kernel (rebased), bc, wc
@@ -976,7 +997,16 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         __syncwarp();
         if (lane == 0) {
             const unsigned old = smem_add_acq_rel(&s_fin[it % (2 * HR_RING)], 1u);
-            if ((old + 1u) % HR_CONSUMERS == 0) red_release_add(&w.stages[t_stage].done, 1u);
+            if ((old + 1u) % HR_CONSUMERS == 0) {
+                hr_stage* st = &w.stages[t_stage & 0x7FFFFFFFu];
+                if (t_stage >> 31) {
+                    // the job's last stage: the tile that completes it stamps the job's end
+                    const unsigned prev = atom_add_release(&st->done, 1u);
+                    if (prev + 1u == st[1].item_begin - st->item_begin) w.jobs[st->job].done_ns = globaltimer();
+                } else {
+                    red_release_add(&st->done, 1u);
+                }
+            }
         }
     }
     flush();

@@ -89,6 +89,7 @@ def load_library():
                                          ctypes.POINTER(P), ctypes.POINTER(P), P]
     lib.hr_set_filter.argtypes = [P, u32, ctypes.POINTER(HrFilter), P]
     lib.hr_check_trace_host.argtypes = [P, u32, P, u64, u64, P]
+    lib.hr_batch_job_times.argtypes = [P, ctypes.POINTER(u64), u32]
     lib.hr_check_trace.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_plain.argtypes = [P, u32, P, u64, P]
     lib.hr_check_trace_kbase.argtypes = [P, u32, P, u64, u32, P]
@@ -247,6 +248,12 @@ class Checker:
             fn = self._lib.hr_check_trace if aggregate else self._lib.hr_check_trace_plain
             rc = fn(self._ctx, region, ptr, n, st)
         self._check(rc, "hr_check_trace")
+
+    def batch_job_times(self, n: int) -> np.ndarray:
+        """Per-job completion times (ns after the batch started) of the last check_batch."""
+        buf = (ctypes.c_uint64 * max(1, n))()
+        self._check(self._lib.hr_batch_job_times(self._ctx, buf, n), "hr_batch_job_times")
+        return np.frombuffer(buf, dtype=np.uint64)[:n].copy()
 
     def check_trace_host(self, region: int, trace, chunk_records: int = 0, stream=None):
         """Queue a check of a trace in host memory (a CPU tensor or a numpy array of

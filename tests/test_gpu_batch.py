@@ -133,3 +133,30 @@ def test_uneven_batch_workload(oracle_mod, hr):
             want = oracle_mod.race_keys(oracle_mod.bruteforce(tr, info["block_dim"]))
             races, status, n_total, _ = ck.report(i)
             assert status == hr.HR_OK and hr.race_keys(races) == want, i
+
+
+def test_batch_job_completion_times(hr):
+    """hr_batch_job_times: one device-clock completion time per job of the last
+    batch; an empty trace reads 0; no job ends after the batch's own span, and
+    the last one ends late in it (stages interleave wave-major, so the job with
+    the most waves tends to end last, not the longest)."""
+    import torch
+    jobs = mixed_jobs()
+    big, info = tg.gen_global_mix(tg.seed_for(2, 13), n_blocks=64)
+    regions = [dict(n_words=nw, block_dim=bd, warp_size=ws) for _, nw, bd, ws in jobs]
+    regions.append(dict(n_words=info["n_words"], block_dim=256))
+    regions.append(dict(n_words=8, block_dim=32))
+    dev = [to_dev(tr) for tr, _, _, _ in jobs] + [to_dev(big), to_dev(big[:0])]
+    with hr.Checker(regions) as ck:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ck.check_batch(list(enumerate(dev)))
+        b.record()
+        torch.cuda.synchronize()
+        span_ns = a.elapsed_time(b) * 1e6
+        t = ck.batch_job_times(len(dev))
+        for i in range(len(dev) - 1):
+            assert ck.report(i)[1] == hr.HR_OK
+    assert t[-1] == 0                                  # the empty trace
+    assert (t[:-1] > 0).all() and t[:-1].max() <= span_ns
+    assert t[:-1].max() >= 0.5 * span_ns
