@@ -574,10 +574,16 @@ def run_gpu(args, rank, world, local_rank):
         cores = host_cores()
         rate, dt, acc = cpu_oracle_rate(trace, info, n_acc, threads=cores)
         rate1, dt1, _ = cpu_oracle_rate(trace, info, n_acc)
+        from oracle import oracle
+        t0 = time.perf_counter()
+        bf = oracle.bruteforce_parallel(trace, info["block_dim"], info["n_words"], threads=cores)
+        dtb = time.perf_counter() - t0
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "whole workload once (%d accesses, %.1f s): serial FSM oracle in C on %d disjoint "
                          "word ranges, one host thread each" % (acc, dt, cores),
-                "single_core": {"value": rate1, "cores": 1, "seconds": dt1}}
+               "single_core": {"value": rate1, "cores": 1, "seconds": dt1},
+               "bruteforce_all_cores": {"value": n_acc / dtb, "cores": cores, "seconds": dtb,
+                                        "racy_words": int(len(bf))}}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

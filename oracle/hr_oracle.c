@@ -353,6 +353,43 @@ int64_t hro_bruteforce(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_
     return nr;
 }
 
+/* The brute force restricted to words in [lo, hi): the same groups and forms,
+ * so the union over disjoint ranges is hro_bruteforce's result (used to run the
+ * definition on several host cores, one range per thread). */
+int64_t hro_bruteforce_range(const hro_rec* r, uint64_t n, uint32_t block_dim, uint32_t warp_size,
+                             uint64_t pair_limit, uint64_t lo, uint64_t hi, hro_race* out, uint64_t cap)
+{
+    uint64_t m = 0;
+    for (uint64_t i = 0; i < n; i++) m += is_access(r[i].op) && r[i].word >= lo && r[i].word < hi;
+    uint64_t* key = (uint64_t*)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint64_t* idx = (uint64_t*)malloc((m ? m : 1) * sizeof(uint64_t));
+    uint64_t j = 0;
+    for (uint64_t i = 0; i < n; i++)
+        if (is_access(r[i].op) && r[i].word >= lo && r[i].word < hi) {
+            key[j] = ((uint64_t)r[i].kernel << 32) | r[i].word;
+            idx[j] = i;
+            j++;
+        }
+    radix_sort(key, idx, m, 48);
+    int64_t nr = 0;
+    uint64_t s = 0;
+    while (s < m) {
+        uint64_t e = s + 1;
+        while (e < m && key[e] == key[s]) e++;
+        hro_race rr;
+        memset(&rr, 0, sizeof rr);
+        int racy = (e - s <= pair_limit) ? group_pairwise(r, idx + s, e - s, block_dim, warp_size, &rr)
+                                         : group_counts(r, idx + s, e - s, block_dim, warp_size, &rr);
+        if (racy) {
+            if ((uint64_t)nr < cap) out[nr] = rr;
+            nr++;
+        }
+        s = e;
+    }
+    free(key); free(idx);
+    return nr;
+}
+
 /* --------------------------------------- every racy epoch (report mode 1) */
 
 /* Rows for one (kernel, word) group: one per distinct epoch e = max(bc_a, bc_b)

@@ -71,6 +71,8 @@ def _lib():
         lib.hro_validate.restype = ctypes.c_int
         lib.hro_bruteforce.argtypes = [P, u64, u32, u32, u64, P, u64]
         lib.hro_bruteforce.restype = i64
+        lib.hro_bruteforce_range.argtypes = [P, u64, u32, u32, u64, u64, u64, P, u64]
+        lib.hro_bruteforce_range.restype = i64
         lib.hro_bruteforce_epochs.argtypes = [P, u64, u32, u32, u64, P, u64]
         lib.hro_bruteforce_epochs.restype = i64
         lib.hro_group_check.argtypes = [P, P, u64, u32, u32, ctypes.c_int, P]
@@ -118,6 +120,35 @@ def bruteforce(trace, block_dim: int, warp_size: int = 32, pair_limit: int = 409
         if n <= cap:
             return out[:n]
         cap = int(n)
+
+
+def bruteforce_parallel(trace, block_dim: int, n_words: int, warp_size: int = 32, pair_limit: int = 4096,
+                        threads: int = 0) -> np.ndarray:
+    """bruteforce over `threads` disjoint word ranges at once (one host thread
+    each; the C calls release the GIL).  The same rows as bruteforce, in range
+    order.  threads=0: every core this process may run on.  The trace is not
+    validated here (bruteforce does that)."""
+    from concurrent.futures import ThreadPoolExecutor
+    rec = _as_records(trace)
+    if threads <= 0:
+        threads = len(os.sched_getaffinity(0))
+    threads = max(1, min(threads, n_words))
+    bounds = [n_words * i // threads for i in range(threads + 1)]
+
+    def run(i):
+        cap = 1 << 12
+        while True:
+            out = np.zeros(cap, RACE_DT)
+            n = _lib().hro_bruteforce_range(_ptr(rec), len(rec), block_dim, warp_size, pair_limit, bounds[i],
+                                            bounds[i + 1], _ptr(out), cap)
+            if n <= cap:
+                return out[:n]
+            cap = int(n)
+
+    _lib()
+    with ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(run, range(threads)))
+    return np.concatenate(parts) if parts else np.zeros(0, RACE_DT)
 
 
 def bruteforce_epochs(trace, block_dim: int, warp_size: int = 32, pair_limit: int = 4096) -> np.ndarray:

@@ -170,3 +170,15 @@ def test_every_epoch_count_form_equals_pairwise(oracle_mod):
     a = O.bruteforce_epochs(tr, info["block_dim"])
     b = O.bruteforce_epochs(tr, info["block_dim"], pair_limit=1)
     assert O.race_keys(a) == O.race_keys(b) and len(a) > len(O.bruteforce(tr, info["block_dim"]))
+
+
+@pytest.mark.parametrize("threads", [1, 4, 7])
+def test_word_partitioned_bruteforce_equals_bruteforce(oracle_mod, threads):
+    """Word ranges split the (kernel, word) groups: the same rows as one run."""
+    O = oracle_mod
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 15), inject=True, n_blocks=4)
+    a = O.bruteforce(tr, 256)
+    b = O.bruteforce_parallel(tr, 256, info["n_words"], threads=threads)
+    assert len(a) == len(b) and O.race_keys(a) == O.race_keys(b)
+    key = lambda r: sorted(zip(r["kernel"].tolist(), r["word"].tolist(), r["ops_mask"].tolist()))
+    assert key(a) == key(b)
