@@ -264,11 +264,12 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     w.test_flags = ctx->test_flags;
     unsigned variant = aggregate ? ctx->variant : (ctx->variant | 1u);  // odd ids do not aggregate
     if (r.desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
+    unsigned launches = 0;
     cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, variant, s,
-                                   ctx->profile ? pc.mid : nullptr);
+                                   ctx->profile ? pc.mid : nullptr, &launches);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
-        pc.launches = HR_LAUNCHES_PER_CHECK;
+        pc.launches = launches;
         ctx->calls.push_back(pc);
     }
     if (e == cudaSuccess) e = mark_done(r, s);
@@ -431,11 +432,12 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
     unsigned variant = ctx->variant;
     for (const auto& d : js)
         if (ctx->regions[d.region].desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
+    unsigned launches = 0;
     cudaError_t e = hr_launch_jobs(ctx->d_regions, w, js.data(), (unsigned)js.size(), ctx->d_table, variant, s,
-                                   ctx->profile ? pc.mid : nullptr);
+                                   ctx->profile ? pc.mid : nullptr, &launches);
     if (ctx->profile) {
         cudaEventRecord(pc.end, s);
-        pc.launches = HR_LAUNCHES_PER_CHECK;
+        pc.launches = launches;
         ctx->calls.push_back(pc);
     }
     for (auto& d : js)

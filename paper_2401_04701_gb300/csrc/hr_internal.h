@@ -220,13 +220,15 @@ constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;
 // kernel launch helpers (hr_kernels.cu)
 // Check n_jobs jobs (1..HR_MAX_BATCH) on the regions of d_regions with the
 // scratch w.  Jobs must name distinct regions and hold n > 0 records.
+// *launches (if not NULL) receives the kernels launched: 2 for a small single
+// trace (one-CTA pre-pass), 5 otherwise.
 cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_jobd* jobs, unsigned n_jobs,
                            const unsigned char* d_table, unsigned variant, cudaStream_t stream,
-                           cudaEvent_t before_check);
+                           cudaEvent_t before_check, unsigned* launches = nullptr);
 // interval size and count for a job of n records when it may use up to budget intervals
 void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int);
 int hr_check_grid_size(unsigned variant);
-constexpr unsigned HR_LAUNCHES_PER_CHECK = 5;  // pre-pass (4) + checker (1)
+constexpr unsigned HR_SMALL_INTERVALS = 4096;  // single traces of at most this many pre-pass intervals take the one-CTA pre-pass
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
 cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long shadow_bytes,
                             cudaStream_t stream);

@@ -149,7 +149,9 @@ __device__ unsigned long long block_exclusive_scan(unsigned long long v, unsigne
     return before;
 }
 
-__global__ void __launch_bounds__(1024) hr_scan_counts(hr_work w, unsigned total_int, hr_region_dev* regions)
+// Exclusive scan of the interval counts into wave offsets, each job's wave range,
+// the control block's reset (one CTA of 1024 threads).
+__device__ void scan_counts_body(hr_work& w, unsigned total_int, hr_region_dev* regions)
 {
     const unsigned per = (total_int + 1023) / 1024;
     const unsigned b = threadIdx.x * per, e = min(total_int, b + per);
@@ -180,6 +182,11 @@ __global__ void __launch_bounds__(1024) hr_scan_counts(hr_work w, unsigned total
         w.ctl->n_stages = 0;
         w.ctl->n_waves = over ? 0u : (unsigned)total;
     }
+}
+
+__global__ void __launch_bounds__(1024) hr_scan_counts(hr_work w, unsigned total_int, hr_region_dev* regions)
+{
+    scan_counts_body(w, total_int, regions);
 }
 
 template <unsigned CAP>
@@ -358,6 +365,99 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
         stages_one_job(w, regions);
     else
         stages_many_jobs(w, regions);
+}
+
+// The whole pre-pass of one small trace (at most HR_SMALL_INTERVALS intervals)
+// in one CTA: the four kernels above as phases separated by block barriers, so
+// a small check costs two launches instead of five.  Phase (a) finds the
+// intervals holding a wave boundary (one lane per interval, two keys each),
+// (b) counts each one's boundaries (a warp per interval), (c) scans the counts,
+// (d) writes the wave table, (e) builds the stages.
+__global__ void __launch_bounds__(1024) hr_prepass_small(const JobParams<1> P, unsigned total_int, hr_work w,
+                                                         hr_region_dev* regions)
+{
+    __shared__ unsigned s_list[HR_SMALL_INTERVALS];  // intervals holding a boundary
+    __shared__ unsigned s_n;
+    const unsigned lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const hr_jobd& jb = P.job[0];
+    const unsigned long long n = jb.n, kb = jb.kb, G = jb.G;
+    if (threadIdx.x == 0) {
+        hr_jobd j0 = jb;
+        j0.done_ns = 0;
+        w.jobs[0] = j0;
+        w.ctl->n_jobs = 1;
+        w.ctl->t0_ns = globaltimer();
+        s_n = 0;
+    }
+    __syncthreads();
+    // (a)
+    for (unsigned i = threadIdx.x; i < total_int; i += blockDim.x) {
+        const unsigned long long beg = (unsigned long long)i * G, end = min(n, beg + G);
+        if (i == 0 || key_at(jb.trace, beg - 1, kb) != key_at(jb.trace, end - 1, kb))
+            s_list[atomicAdd(&s_n, 1u)] = i;
+        else
+            w.counts[i] = 0;
+    }
+    __syncthreads();
+    const unsigned n_need = s_n;
+    // (b)
+    for (unsigned q = warp; q < n_need; q += blockDim.x >> 5) {
+        const unsigned i = s_list[q];
+        const unsigned long long beg = (unsigned long long)i * G, end = min(n, beg + G);
+        unsigned cnt = 0;
+        bool bad = false;
+#pragma unroll 8
+        for (unsigned long long c = beg; c < end; c += 32) {
+            const unsigned long long p = c + lane;
+            if (p < end) {
+                const unsigned long long k = key_at(jb.trace, p, kb);
+                if (p == 0) {
+                    cnt++;
+                } else {
+                    const unsigned long long kp = key_at(jb.trace, p - 1, kb);
+                    cnt += k != kp;
+                    bad |= k < kp;
+                }
+            }
+        }
+        if (bad) hr_set_error(&regions[jb.region].error, HR_ERR_ORDER);
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0) w.counts[i] = cnt;
+    }
+    __syncthreads();
+    // (c)
+    scan_counts_body(w, total_int, regions);
+    __syncthreads();
+    // (d)
+    const unsigned n_waves = w.ctl->n_waves;
+    for (unsigned q = warp; q < n_need && n_waves; q += blockDim.x >> 5) {
+        const unsigned i = s_list[q];
+        const unsigned long long beg = (unsigned long long)i * G, end = min(n, beg + G);
+        const unsigned next = (i + 1 < total_int) ? w.counts[i + 1] : n_waves;
+        unsigned off = w.counts[i];
+        if (off == next) continue;
+        for (unsigned long long c = beg; c < end; c += 32) {
+            const unsigned long long p = c + lane;
+            bool is_b = false;
+            unsigned long long k = 0;
+            if (p < end) {
+                k = key_at(jb.trace, p, kb);
+                is_b = (p == 0) || k != key_at(jb.trace, p - 1, kb);
+            }
+            const unsigned mask = __ballot_sync(0xffffffffu, is_b);
+            if (is_b) {
+                const unsigned slot = off + __popc(mask & ((1u << lane) - 1u));
+                if (slot < n_waves) {
+                    w.wave_start[slot] = p;
+                    w.wave_key[slot] = k;
+                }
+            }
+            off += __popc(mask);
+        }
+    }
+    __syncthreads();
+    // (e)
+    stages_one_job(w, regions);
 }
 
 // ------------------------------------------------------------ the FSM checker
@@ -1105,7 +1205,7 @@ static void launch_prepass(const JobParams<CAP>& P, unsigned total_int, hr_regio
 
 cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const hr_jobd* jobs, unsigned n_jobs,
                            const unsigned char* d_table, unsigned variant, cudaStream_t stream,
-                           cudaEvent_t before_check)
+                           cudaEvent_t before_check, unsigned* launches)
 {
     if (variant > HR_EVERY_EPOCH_VARIANT) return cudaErrorInvalidValue;
     hr_work w = w_in;
@@ -1115,11 +1215,17 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
     if (n_jobs == 0 || n_jobs > HR_MAX_BATCH || n_jobs > w.max_jobs) return cudaErrorInvalidValue;
     const unsigned total_int = jobs[n_jobs - 1].int_begin + jobs[n_jobs - 1].n_int;
     if (total_int > w.max_intervals) return cudaErrorInvalidValue;
+    unsigned prepass_launches = 4;
     if (n_jobs == 1) {
         JobParams<1> P;
         P.n = 1;
         P.job[0] = jobs[0];
-        launch_prepass(P, total_int, d_regions, w, stream);
+        if (total_int <= HR_SMALL_INTERVALS) {  // a small trace: the whole pre-pass in one CTA
+            hr_prepass_small<<<1, 1024, 0, stream>>>(P, total_int, w, d_regions);
+            prepass_launches = 1;
+        } else {
+            launch_prepass(P, total_int, d_regions, w, stream);
+        }
     } else {
         static thread_local JobParams<HR_MAX_BATCH> P;  // 24 KB: off the stack; copied into the launch
         P.n = n_jobs;
@@ -1127,6 +1233,7 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
         launch_prepass(P, total_int, d_regions, w, stream);
     }
     if (before_check) cudaEventRecord(before_check, stream);
+    if (launches) *launches = prepass_launches + 1;
     switch (variant) {
     case 0: launch_variant<true, 4, 8>(grid, d_regions, w, d_table, stream); break;
     case 1: launch_variant<false, 4, 8>(grid, d_regions, w, d_table, stream); break;
