@@ -610,7 +610,7 @@ def run_gpu(args, rank, world, local_rank):
     }
     if cpu:
         line["cpu_baseline"] = cpu
-    if default:
+    if default and not args.no_mode_lines:
         line["compact_shadow"] = compact_shadow_workload(dev, d_trace, info, n_acc, n_sync, best, p_hbm)
         line["every_epoch_reports"] = every_epoch_workload(dev, d_trace, info, n_acc, n_sync, p_hbm)
     if not args.no_instrumented:
@@ -641,6 +641,8 @@ def main():
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the checker kernel variant instead of autotuning")
+    ap.add_argument("--no-mode-lines", action="store_true",
+                    help="skip the compact-shadow and every-epoch lines (profiling runs)")
     ap.add_argument("--workload", default="global", choices=["global", "powerlaw", "tree"],
                     help="time another workload instead of the global mix (parity is in the tests)")
     ap.add_argument("--log2-vertices", type=int, default=22, help="power-law workload size")
