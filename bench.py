@@ -49,8 +49,9 @@ ALG_BYTES_PER_SYNC = 16     # a barrier record is streamed, not an access
 ALG_BYTES_PER_ACCESS_COMPACT = 24  # 16 B record + 4 B shadow read + 4 B shadow write
 
 
-KERNEL_SOURCES = ("paper_2401_04701_gb300/csrc/hr_kernels.cu", "paper_2401_04701_gb300/csrc/hr_internal.h",
-                  "include/hirace_device.cuh")
+KERNEL_SOURCES = ("paper_2401_04701_gb300/csrc/hr_kernels.cu", "paper_2401_04701_gb300/csrc/hr_binned.cu",
+                  "paper_2401_04701_gb300/csrc/hr_internal.h", "include/hirace_device.cuh")
+BINNED_KERNELS = "hr_bin_count, hr_bin_scan_sums, hr_bin_scan, hr_bin_scatter, hr_bin_segments"
 
 
 def kernel_sources_sha():
@@ -62,17 +63,27 @@ def kernel_sources_sha():
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per checker launch from the committed ncu capture, or None when
-    the kernel sources changed since it was taken."""
+def measured_traffic(variant):
+    """DRAM bytes of one check (the kernels after the pre-pass) with this checker
+    variant, from the committed ncu capture; None when the kernel sources changed
+    since it was taken or the variant was not captured."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             t = json.load(f)
-        if t.get("kernel_sources_sha256") == kernel_sources_sha():
-            return int(t["dram_bytes_read"]) + int(t["dram_bytes_write"])
+        e = t.get("checks", {}).get(str(variant))
+        if e and t.get("kernel_sources_sha256") == kernel_sources_sha():
+            return int(e["dram_bytes_read"]) + int(e["dram_bytes_write"])
     except Exception:
         pass
     return None
+
+
+def checker_name(variant):
+    """The kernels one check runs after the pre-pass, for the JSON line."""
+    from paper_2401_04701_gb300 import hirace
+    if dict(hirace.variants())[variant]["binned"]:
+        return "binned checker (variant %d): %s" % (variant, BINNED_KERNELS)
+    return "hr_check_kernel variant %d" % variant
 
 
 def peaks():
@@ -596,8 +607,8 @@ def run_gpu(args, rank, world, local_rank):
                        len(trace) * 16 / 1e9, info["n_words"] * 8 >> 20),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": p_hbm, "unit": "GB/s",
-                     "frac": achieved / p_hbm, "traffic": measured_traffic() if default else None,
-                     "kernel": "hr_check_kernel variant %d" % best,
+                     "frac": achieved / p_hbm, "traffic": measured_traffic(best) if default else None,
+                     "kernel": checker_name(best),
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),

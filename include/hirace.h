@@ -319,10 +319,19 @@ hr_status hr_destroy(hr_ctx* ctx);
 
 /*
  * Kernel variants and the autotuner (no paper counterpart; the tile schedule
- * of the checker).  A variant fixes the consumer warps per CTA, the records
- * each consumer lane takes per tile and whether lanes on the same word are
- * aggregated; even ids aggregate and the odd id after each is the same shape
- * without aggregation.  hr_autotune checks the given trace on `region` with
+ * of the checker).  Ids 0..5 are shapes of the per-wave checker: a variant
+ * fixes the consumer warps per CTA, the records each consumer lane takes per
+ * tile and whether lanes on the same word are aggregated; even ids aggregate
+ * and the odd id after each is the same shape without aggregation.  Id 6 is the
+ * binned checker, which hr_variant_desc reports with zero records per lane and
+ * zero consumer warps: the accesses are moved into (4096-word shadow segment,
+ * wave) buckets and one CTA per segment applies them to a shared-memory copy of
+ * the segment, wave by wave.  It takes single-trace checks of regions of at
+ * most 2^26 words with at most 256 waves per call; batches, and calls it cannot
+ * take, run the per-wave checker of id 3.  Its first check on a region
+ * allocates the region's bucket tables (about 400 bytes per segment and SM) and
+ * an 8-byte-per-record access buffer, so do that check before capturing calls
+ * into a CUDA graph.  Its shared-memory CAS loops are bounded by the same cap.  hr_autotune checks the given trace on `region` with
  * every variant (reset before each run, a warm-up then a timed run on
  * `stream`, synchronous), keeps the fastest for this context's later checks,
  * writes it to *best and the per-variant milliseconds to ms[0..ms_cap), and

@@ -25,6 +25,8 @@ struct RegionHost {
     bool owns_ring = true;
     cudaEvent_t done = nullptr;           // recorded after every call on the region
     bool captured = false;                // work was queued inside a stream capture
+    void* bin_mem = nullptr;              // binned checker tables (allocated by its first check)
+    hr_bin bin{};                         // carved out of bin_mem; bin.out is its own allocation
 };
 
 // Record the region's completion event, unless the stream is being captured
@@ -113,6 +115,8 @@ static void free_ctx(hr_ctx* c)
         if (r.owns_shadow) cudaFree(r.shadow);
         if (r.owns_ring) cudaFree(r.ring);
         cudaFree(r.work_mem);
+        cudaFree(r.bin_mem);
+        cudaFree(r.bin.out);
     }
     for (auto* v : {&c->calls, &c->spare})
         for (auto& p : *v) {
@@ -238,6 +242,56 @@ extern "C" hr_status hr_init_with_buffers(hr_ctx** out, const hr_region_desc* re
     return init_impl(out, regions, n_regions, report_capacity, shadows, rings, stream);
 }
 
+// The binned checker's tables for the region's current size and an access
+// buffer of n records.  Growing them waits for the device (work in flight may
+// still use the old buffers); the first binned check of a region allocates.
+static hr_status ensure_bin(RegionHost& r, uint64_t n, cudaStream_t s)
+{
+    (void)s;
+    const unsigned n_seg = (unsigned)((r.desc.n_words + HR_BIN_SEG - 1) / HR_BIN_SEG);
+    cudaError_t e = cudaSuccess;
+    if (!r.bin_mem || r.bin.seg_cap < n_seg) {
+        const unsigned cap = (unsigned)((r.capacity + HR_BIN_SEG - 1) / HR_BIN_SEG);
+        unsigned clusters = 0, sub = 0;
+        hr_bin_shape(&clusters, &sub);
+        const unsigned slices = clusters * sub;
+        const unsigned part_cap = HR_BIN_MAX_WAVES + slices - 1;
+        const size_t bytes = hr_bin_table_bytes(cap, part_cap);
+        if (r.bin_mem) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaFree(r.bin_mem);
+        r.bin_mem = nullptr;
+        r.bin.seg_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&r.bin_mem, bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
+        const size_t ent = (size_t)cap * part_cap;
+        char* p = (char*)r.bin_mem;
+        r.bin.table = (unsigned*)p;
+        p += a(ent * 4);
+        r.bin.sums = (unsigned*)p;
+        p += a((ent / HR_BIN_SCAN + 1) * 4);
+        r.bin.part_wave = (unsigned*)p;
+        p += a((size_t)part_cap * 4);
+        r.bin.clear = (unsigned char*)p;
+        r.bin.seg_cap = cap;
+        r.bin.part_cap = part_cap;
+        r.bin.clusters = clusters;
+        r.bin.sub = sub;
+        r.bin.slices = slices;
+    }
+    if (r.bin.out_cap < n) {
+        if (r.bin.out) e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaFree(r.bin.out);
+        r.bin.out = nullptr;
+        r.bin.out_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&r.bin.out, n * sizeof(uint2) + 16);
+        if (e != cudaSuccess) return cuda_status(e);
+        r.bin.out_cap = n;
+    }
+    r.bin.n_seg = n_seg;
+    return HR_OK;
+}
+
 static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_trace, uint64_t n,
                               uint32_t kernel_base, hr_stream_t stream, bool aggregate)
 {
@@ -262,8 +316,17 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
     w.test_flags = ctx->test_flags;
-    unsigned variant = aggregate ? ctx->variant : (ctx->variant | 1u);  // odd ids do not aggregate
+    unsigned variant = ctx->variant;
+    if (!aggregate && variant < HR_N_SHAPES) variant |= 1u;  // odd ids do not aggregate (nor does the binned one)
     if (r.desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
+    // 32-bit bucket offsets; segment histograms in shared memory
+    if (variant == HR_BIN_VARIANT && (n >= (1ull << 32) || r.desc.n_words > (uint64_t)HR_BIN_MAX_SEGS * HR_BIN_SEG))
+        variant = HR_BIN_FALLBACK;
+    if (variant == HR_BIN_VARIANT) {
+        const hr_status bs = ensure_bin(r, n, s);
+        if (bs != HR_OK) return bs;
+        w.bin = r.bin;
+    }
     unsigned launches = 0;
     cudaError_t e = hr_launch_jobs(ctx->d_regions, w, &job, 1, ctx->d_table, variant, s,
                                    ctx->profile ? pc.mid : nullptr, &launches);
@@ -429,7 +492,7 @@ extern "C" hr_status hr_check_batch(hr_ctx* ctx, const hr_job* jobs, uint32_t n_
     hr_work w = ctx->batch;
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
-    unsigned variant = ctx->variant;
+    unsigned variant = ctx->variant == HR_BIN_VARIANT ? HR_BIN_FALLBACK : ctx->variant;  // not for batches
     for (const auto& d : js)
         if (ctx->regions[d.region].desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
     unsigned launches = 0;
@@ -588,9 +651,10 @@ extern "C" hr_status hr_variant_desc(uint32_t id, uint32_t* aggregate, uint32_t*
                                      uint32_t* consumer_warps)
 {
     if (id >= HR_N_VARIANTS) return HR_ERR_INVALID;
-    if (aggregate) *aggregate = (uint32_t)HR_VARIANTS[id].aggregate;
-    if (records_per_lane) *records_per_lane = (uint32_t)HR_VARIANTS[id].rpl;
-    if (consumer_warps) *consumer_warps = (uint32_t)HR_VARIANTS[id].consumers;
+    const bool shape = id < HR_N_SHAPES;  // else the binned checker: all zero
+    if (aggregate) *aggregate = shape ? (uint32_t)HR_VARIANTS[id].aggregate : 0u;
+    if (records_per_lane) *records_per_lane = shape ? (uint32_t)HR_VARIANTS[id].rpl : 0u;
+    if (consumer_warps) *consumer_warps = shape ? (uint32_t)HR_VARIANTS[id].consumers : 0u;
     return HR_OK;
 }
 

@@ -1,0 +1,754 @@
+// hr_binned.cu - the binned trace checker (variant HR_BIN_VARIANT, sm_103a).
+//
+// The per-wave checker (hr_kernels.cu) applies each wave's accesses to the
+// shadow in HBM and orders the waves across the whole GPU with stage counters;
+// every access then costs a random read-modify-write of an 8-byte shadow value
+// and every wave boundary drains the GPU.  This checker organises the same
+// work around the shadow instead.  The region's shadow is cut into segments of
+// HR_BIN_SEG words, each access of the trace is moved into the bucket of its
+// (segment, wave), and one CTA per segment holds that segment's shadow in
+// shared memory and applies its buckets in wave order, with a block barrier
+// between waves.
+//
+// Why this is the same computation: Algorithm 1 folds the accesses of a word
+// into its shadow value one at a time, and Sec. II-B orders two accesses only
+// through a barrier or a kernel end, so every pair inside one wave (records of
+// equal (kernel, bc, wc)) is unordered and any order of a wave's accesses is a
+// valid execution order; processing the waves in order keeps every ordered
+// pair in order.  A word's accesses all land in one segment, and the segment's
+// CTA applies its buckets in wave order, so each word sees exactly what the
+// per-wave checker would show it.  Buckets need no stable order, so accesses
+// are appended with atomics.
+//
+// Launches after the shared pre-pass (wave table and stage list):
+//   1. hr_bin_count     : one CTA per SM takes a contiguous slice of the trace;
+//                         for each part (the slice's records of one wave) it
+//                         validates the records (the per-wave checker's checks
+//                         and errors) and counts the accesses per segment in a
+//                         shared-memory histogram, then writes the histogram
+//                         into the table column of that part
+//   2. hr_bin_scan_sums : the sum of each block of the table; the per-wave
+//                         shadow-clear flags; the "binned" flag
+//   3. hr_bin_scan      : exclusive scan of the table (segment-major, parts in
+//                         trace order) into bucket offsets
+//   4. hr_bin_scatter   : clusters of CTAs walk the same slices wave by wave;
+//                         each access, packed to 8 bytes (tid, op, word within
+//                         the segment), goes to its bucket's next slot (cursors
+//                         in distributed shared memory: no global atomics)
+//   5. hr_bin_segments  : per segment: shadow -> shared memory, its accesses in
+//                         wave order with a shared-memory CAS per access, races
+//                         appended to the region's ring, shadow written back
+// A check with more than HR_BIN_MAX_WAVES waves is not binned: the flag stays
+// clear and the per-wave checker launched after these kernels does the work.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include "hr_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr unsigned STREAM_THREADS = 1024;      // threads of the two streaming passes (one CTA per SM)
+constexpr unsigned STREAM_R = 4;               // records each streaming thread loads per step
+constexpr unsigned STREAM_STEP = STREAM_THREADS * STREAM_R;
+constexpr unsigned SCAN_THREADS = 1024;
+
+// whether this check is one the binned checker takes (read from the pre-pass
+// results; every kernel below decides the same way)
+__device__ __forceinline__ bool bin_fits(const hr_ctl* c)
+{
+    return c->n_jobs == 1 && c->total_items > 0 && c->n_waves >= 1 && c->n_waves <= HR_BIN_MAX_WAVES;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async8(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// wait until at most N of this thread's copy groups are still in flight
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Records of a streaming step: thread tx owns slots j * STREAM_THREADS + tx of
+// a step (the same slots it processes), so a thread's copies are visible to it
+// after its own wait and no block barrier is needed; two steps are in flight.
+__device__ __forceinline__ void stream_issue(uint4* tile, const hr_record* trace, unsigned long long base,
+                                             unsigned long long end)
+{
+#pragma unroll
+    for (unsigned j = 0; j < STREAM_R; ++j) {
+        const unsigned long long i = base + j * STREAM_THREADS + threadIdx.x;
+        if (i < end) cp_async16(&tile[j * STREAM_THREADS + threadIdx.x], trace + i);
+    }
+    cp_async_commit();
+}
+
+// One record classified for the binned checker: the checks of the per-wave
+// checker (wave key, op, filter, range, packing), its segment and packed form.
+struct BinAcc {
+    unsigned seg;
+    uint2 rec;
+    unsigned err;
+    bool act;
+};
+
+// clocks_fit: the wave's bc and wc fit the region's packing (hr_fits without the tid)
+__device__ __forceinline__ BinAcc bin_decode(const uint4 v, bool in, unsigned long long key, unsigned kb,
+                                             const hr_geom& g, const hr_filter& f, bool filtering,
+                                             unsigned long long n_words, bool clocks_fit)
+{
+    BinAcc r{0u, make_uint2(0u, 0u), 0u, false};
+    const unsigned kern = (unsigned)(key >> 32), bcwc = (unsigned)key;
+    const unsigned op = (v.w >> 16) & 0xFFu;
+    const unsigned flags = v.w >> 24;
+    const bool same_wave = v.z == bcwc && (v.w & 0xFFFFu) + kb == kern;
+    bool a = in && op <= HR_A;
+    unsigned widx = v.x;
+    bool mon = true;
+    if (filtering && a && same_wave) {
+        unsigned long long ix = v.x;
+        mon = hr_monitored(f, g, v.y, v.x, &ix);
+        widx = (unsigned)ix;
+    }
+    if (in) {
+        if (!same_wave) r.err = HR_ERR_ORDER;
+        else if (op > HR_SYNCWARP || (op == HR_SYNCWARP && (flags & HR_RECFLAG_PARTIAL_MASK)))
+            r.err = HR_ERR_UNSUPPORTED;
+        else if (a && mon && widx >= n_words)
+            r.err = HR_ERR_RANGE;
+    }
+    a = a && same_wave && mon && widx < n_words;
+    if (a && !(clocks_fit && (g.shadow_bytes != 4 || (v.y >> g.tid_bits) == 0))) {
+        r.err = HR_ERR_CLOCK_OVERFLOW;
+        a = false;
+    }
+    r.act = a;
+    r.seg = widx >> HR_BIN_SEG_SHIFT;
+    r.rec = make_uint2(v.y, (op << 16) | (widx & (HR_BIN_SEG - 1u)));
+    return r;
+}
+
+__device__ __forceinline__ unsigned block_sum(unsigned v, unsigned* s_warp)
+{
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if (lane == 0) s_warp[wid] = v;
+    __syncthreads();
+    unsigned t = 0;
+    for (unsigned i = 0; i < (blockDim.x >> 5); ++i) t += s_warp[i];
+    __syncthreads();
+    return t;
+}
+
+// exclusive scan of one value per thread over the block (a multiple of 32 threads)
+__device__ __forceinline__ unsigned block_exclusive(unsigned v, unsigned* s_warp)
+{
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    if (lane == 31) s_warp[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned s = lane < nw ? s_warp[lane] : 0u;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= (unsigned)o) s += y;
+        }
+        s_warp[lane] = s;
+    }
+    __syncthreads();
+    const unsigned before = (wid ? s_warp[wid - 1] : 0u) + x - v;
+    __syncthreads();
+    return before;
+}
+
+// Shared-memory state of the two streaming passes: the job's wave table, this
+// CTA's slice and its first part, and a per-segment array (histogram or cursors).
+struct StreamSmem {
+    unsigned long long start[HR_BIN_MAX_WAVES + 1];  // first record of each wave; start[W] = n
+    unsigned long long key[HR_BIN_MAX_WAVES];        // rebased wave keys
+    unsigned s_warp[32];
+    unsigned p0, np, w0, n_parts;
+    unsigned long long a, b;                         // this CTA's records [a, b)
+    unsigned seg[HR_BIN_MAX_SEGS];
+    uint4 tile[2][STREAM_STEP];                      // two steps of records in flight
+};
+constexpr size_t STREAM_SMEM = sizeof(StreamSmem);
+
+// first wave holding record i (binary search)
+__device__ __forceinline__ unsigned wave_find(const StreamSmem& S, unsigned W, unsigned long long i)
+{
+    unsigned lo = 0, hi = W;
+    while (hi - lo > 1) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (S.start[mid] <= i) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Count slice c: the trace is cut into one slice per scatter cluster, and each
+// of those into `sub` count slices, so a cluster's records are the union of
+// consecutive count slices.
+__device__ __forceinline__ void count_slice(unsigned long long n, const hr_bin& bin, unsigned c,
+                                            unsigned long long* a, unsigned long long* b)
+{
+    const unsigned long long per_cl = (n + bin.clusters - 1) / bin.clusters;
+    const unsigned long long per_sub = (per_cl + bin.sub - 1) / bin.sub;
+    const unsigned cl = c / bin.sub, j = c % bin.sub;
+    const unsigned long long A = min(n, cl * per_cl), B = min(n, A + per_cl);
+    *a = min(B, A + j * per_sub);
+    *b = min(B, *a + per_sub);
+}
+
+// The wave table, then the slices of all count CTAs (thread c < slices
+// measures slice c), their parts and this CTA's first part.
+__device__ void stream_prologue(const hr_work& w, const hr_jobd& jb, unsigned W, StreamSmem& S)
+{
+    for (unsigned i = threadIdx.x; i < W; i += blockDim.x) {
+        S.start[i] = w.wave_start[jb.wave_begin + i];
+        S.key[i] = w.wave_key[jb.wave_begin + i];
+    }
+    if (threadIdx.x == 0) S.start[W] = jb.n;
+    __syncthreads();
+    const unsigned c = threadIdx.x;
+    unsigned np = 0, w0 = 0;
+    unsigned long long a = 0, b = 0;
+    if (c < w.bin.slices) {
+        count_slice(jb.n, w.bin, c, &a, &b);
+        if (a < b) {
+            w0 = wave_find(S, W, a);
+            np = wave_find(S, W, b - 1) - w0 + 1;
+        }
+    }
+    const unsigned before = block_exclusive(np, S.s_warp);
+    if (c == blockIdx.x) {
+        S.p0 = before;
+        S.np = np;
+        S.w0 = w0;
+        S.a = a;
+        S.b = b;
+    }
+    if (c == w.bin.slices - 1) S.n_parts = before + np;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ 1. counts
+
+__global__ void __launch_bounds__(STREAM_THREADS) hr_bin_count(hr_region_dev* __restrict__ regions, hr_work w)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StreamSmem& S = *reinterpret_cast<StreamSmem*>(smem_raw);
+    if (!bin_fits(w.ctl)) return;
+    const unsigned W = w.ctl->n_waves;
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev* rg = regions + jb.region;
+    const hr_geom g = rg->geom;
+    const hr_filter f = rg->filter;
+    const bool filtering = hr_filter_active(f);
+    const unsigned long long n_words = rg->n_words;
+    const unsigned kb = (unsigned)(jb.kb >> 32);
+    const unsigned n_seg = w.bin.n_seg;
+    stream_prologue(w, jb, W, S);
+    const unsigned P = S.n_parts, tx = threadIdx.x, lane = tx & 31;
+    if (blockIdx.x == 0 && tx == 0) w.ctl->bin_parts = P;
+    unsigned err = 0;
+    for (unsigned k = 0; k < S.np; ++k) {
+        const unsigned gw = S.w0 + k, part = S.p0 + k;
+        const unsigned long long pa = max(S.a, S.start[gw]), pb = min(S.b, S.start[gw + 1]);
+        const unsigned long long key = S.key[gw];
+        const bool fit = hr_fits(0u, ((unsigned)key) >> 16, (unsigned)key & 0xFFFFu, g);
+        for (unsigned i = tx; i < n_seg; i += STREAM_THREADS) S.seg[i] = 0u;
+        if (tx == 0) w.bin.part_wave[part] = gw;
+        __syncthreads();
+        if (pa < pb) stream_issue(S.tile[0], jb.trace, pa, pb);
+        unsigned buf = 0;
+        for (unsigned long long base = pa; base < pb; base += STREAM_STEP, buf ^= 1u) {
+            if (base + STREAM_STEP < pb) {
+                stream_issue(S.tile[buf ^ 1u], jb.trace, base + STREAM_STEP, pb);
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+#pragma unroll
+            for (unsigned j = 0; j < STREAM_R; ++j) {
+                const bool in = base + j * STREAM_THREADS + tx < pb;
+                const uint4 v = in ? S.tile[buf][j * STREAM_THREADS + tx] : make_uint4(0u, 0u, 0u, 0u);
+                const BinAcc r = bin_decode(v, in, key, kb, g, f, filtering, n_words, fit);
+                if (r.err) err = r.err;
+                if (r.act) atomicAdd(&S.seg[r.seg], 1u);
+            }
+        }
+        __syncthreads();
+        // the part's column of the table (every entry: the table is dense)
+        for (unsigned i = tx; i < n_seg; i += STREAM_THREADS) w.bin.table[(size_t)i * P + part] = S.seg[i];
+        __syncthreads();
+    }
+    if (err) hr_set_error(&rg->error, err);
+}
+
+// ------------------------------------------------------------ 2-3. scan
+
+__global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan_sums(hr_work w)
+{
+    __shared__ unsigned s_warp[32];
+    if (!bin_fits(w.ctl)) return;
+    if (blockIdx.x == 0) {
+        // a wave's shadow clear is the stage right before its record stage
+        const unsigned n_st = w.ctl->n_stages, wb = w.jobs[0].wave_begin;
+        for (unsigned s = threadIdx.x; s < n_st; s += blockDim.x) {
+            const hr_stage st = w.stages[s];
+            if (st.type == HR_STAGE_RECORDS)
+                w.bin.clear[st.wave - wb] = s > 0 && w.stages[s - 1].type == HR_STAGE_CLEAR;
+        }
+        if (threadIdx.x == 0) w.ctl->binned = 1;
+    }
+    const unsigned long long E = (unsigned long long)w.bin.n_seg * w.ctl->bin_parts;
+    const unsigned long long b0 = (unsigned long long)blockIdx.x * HR_BIN_SCAN;
+    if (b0 >= E) return;
+    unsigned v = 0;
+    for (unsigned long long i = b0 + threadIdx.x; i < min(E, b0 + HR_BIN_SCAN); i += blockDim.x) v += w.bin.table[i];
+    v = block_sum(v, s_warp);
+    if (threadIdx.x == 0) w.bin.sums[blockIdx.x] = v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan(hr_work w)
+{
+    __shared__ unsigned s_warp[32];
+    if (!w.ctl->binned) return;
+    const unsigned long long E = (unsigned long long)w.bin.n_seg * w.ctl->bin_parts;
+    const unsigned long long b0 = (unsigned long long)blockIdx.x * HR_BIN_SCAN;
+    if (b0 >= E) return;
+    unsigned part = 0;
+    for (unsigned i = threadIdx.x; i < blockIdx.x; i += blockDim.x) part += w.bin.sums[i];
+    const unsigned base = block_sum(part, s_warp);
+    constexpr unsigned PER = HR_BIN_SCAN / SCAN_THREADS;
+    const unsigned long long i0 = b0 + (unsigned long long)threadIdx.x * PER;
+    unsigned c[PER], local = 0;
+#pragma unroll
+    for (unsigned k = 0; k < PER; ++k) {
+        c[k] = i0 + k < E ? w.bin.table[i0 + k] : 0u;
+        local += c[k];
+    }
+    const unsigned pre = block_exclusive(local, s_warp);
+    unsigned run = base + pre;
+#pragma unroll
+    for (unsigned k = 0; k < PER; ++k) {
+        if (i0 + k < E) {
+            w.bin.table[i0 + k] = run;
+            run += c[k];
+        }
+    }
+    if (i0 < E && i0 + PER >= E) w.ctl->bin_total = run;  // the thread holding the last entry
+}
+
+// ------------------------------------------------------------ 4. scatter
+//
+// Clusters of HR_BIN_CLUSTER CTAs; a cluster's slice is the slices of its CTAs
+// in the count pass, so a (cluster, wave) covers consecutive parts of the
+// table and owns one contiguous range per segment, starting at the table entry
+// of its first part.  The cluster walks its waves in order; for each, the
+// segment cursors are spread over the cluster's shared memory (segment s on
+// rank s % HR_BIN_CLUSTER) and every CTA appends its share of the wave's
+// records with atomics on those cursors (distributed shared memory).  One
+// bucket range per cluster is being filled at a time, so L2 holds one partly
+// written sector per (cluster, segment) and merges the 8-byte stores.
+
+constexpr unsigned CL = HR_BIN_CLUSTER;
+constexpr unsigned SCATTER_R = 4;  // records per thread per step: their atomics are in flight together
+
+struct ScatterSmem {
+    unsigned long long start[HR_BIN_MAX_WAVES + 1];
+    unsigned long long key[HR_BIN_MAX_WAVES];
+    unsigned s_warp[32];
+    unsigned p0[HR_BIN_MAX_SUB], w0[HR_BIN_MAX_SUB], np[HR_BIN_MAX_SUB];  // the cluster's count slices
+    unsigned cur[HR_BIN_MAX_SEGS / CL];
+};
+constexpr size_t SCATTER_SMEM = sizeof(ScatterSmem);
+
+__global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_THREADS)
+    hr_bin_scatter(hr_region_dev* __restrict__ regions, hr_work w)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
+    cg::cluster_group cluster = cg::this_cluster();
+    if (!w.ctl->binned) return;  // the same for every CTA: no remote access happens
+    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev* rg = regions + jb.region;
+    if (*(volatile unsigned*)&rg->error) return;  // no writer runs now: the same for every CTA
+    const hr_geom g = rg->geom;
+    const hr_filter f = rg->filter;
+    const bool filtering = hr_filter_active(f);
+    const unsigned long long n_words = rg->n_words;
+    const unsigned kb = (unsigned)(jb.kb >> 32);
+    const unsigned n_seg = w.bin.n_seg, tx = threadIdx.x, lane = tx & 31;
+    const unsigned rank = cluster.block_rank(), cl = blockIdx.x / CL, sub = w.bin.sub;
+    for (unsigned i = tx; i < W; i += STREAM_THREADS) {
+        S.start[i] = w.wave_start[jb.wave_begin + i];
+        S.key[i] = w.wave_key[jb.wave_begin + i];
+    }
+    if (tx == 0) S.start[W] = jb.n;
+    __syncthreads();
+    // the count pass's slices and their parts
+    {
+        const unsigned c = tx;
+        unsigned np = 0, w0 = 0;
+        if (c < w.bin.slices) {
+            unsigned long long a, b;
+            count_slice(jb.n, w.bin, c, &a, &b);
+            if (a < b) {
+                unsigned lo = 0, hi = W;
+                while (hi - lo > 1) { const unsigned mid = (lo + hi) >> 1; if (S.start[mid] <= a) lo = mid; else hi = mid; }
+                w0 = lo;
+                hi = W;
+                while (hi - lo > 1) { const unsigned mid = (lo + hi) >> 1; if (S.start[mid] <= b - 1) lo = mid; else hi = mid; }
+                np = lo - w0 + 1;
+            }
+        }
+        const unsigned before = block_exclusive(np, S.s_warp);
+        if (c >= cl * sub && c < (cl + 1) * sub) {
+            S.p0[c - cl * sub] = before;
+            S.w0[c - cl * sub] = w0;
+            S.np[c - cl * sub] = np;
+        }
+        __syncthreads();
+    }
+    const unsigned long long per_cl = (jb.n + w.bin.clusters - 1) / w.bin.clusters;
+    const unsigned long long A = min(jb.n, cl * per_cl), B = min(jb.n, A + per_cl);
+    unsigned w_lo = W, w_hi = 0;  // waves of the cluster's slice
+    for (unsigned r = 0; r < sub; ++r)
+        if (S.np[r]) {
+            w_lo = min(w_lo, S.w0[r]);
+            w_hi = max(w_hi, S.w0[r] + S.np[r]);
+        }
+    const unsigned my_segs = (n_seg + CL - 1 - rank) / CL;  // segments s with s % CL == rank
+    for (unsigned gw = w_lo; gw < w_hi; ++gw) {
+        // the cluster's first part of this wave: the first of its CTAs that met it
+        unsigned fp = 0;
+        for (unsigned r = sub; r-- > 0;)
+            if (S.np[r] && S.w0[r] <= gw && gw < S.w0[r] + S.np[r]) fp = S.p0[r] + (gw - S.w0[r]);
+        for (unsigned i = tx; i < my_segs; i += STREAM_THREADS) S.cur[i] = w.bin.table[(size_t)(i * CL + rank) * P + fp];
+        cluster.sync();  // every cursor is loaded before any CTA adds to it
+        const unsigned long long wa = max(A, S.start[gw]), wb = min(B, S.start[gw + 1]);
+        const unsigned long long span = (wb - wa + CL - 1) / CL;
+        const unsigned long long a = min(wb, wa + rank * span), b = min(wb, a + span);
+        const unsigned long long key = S.key[gw];
+        const bool fit = hr_fits(0u, ((unsigned)key) >> 16, (unsigned)key & 0xFFFFu, g);
+        for (unsigned long long base = a; base < b; base += STREAM_STEP) {
+            uint4 v[SCATTER_R];  // every record of the step in flight at once
+#pragma unroll
+            for (unsigned j = 0; j < SCATTER_R; ++j) {
+                const unsigned long long i = base + j * STREAM_THREADS + tx;
+                v[j] = i < b ? __ldcs(reinterpret_cast<const uint4*>(jb.trace + i)) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            uint2 rec[SCATTER_R];
+            unsigned pos[SCATTER_R], grp[SCATTER_R];
+            bool act[SCATTER_R];
+#pragma unroll
+            for (unsigned j = 0; j < SCATTER_R; ++j) {
+                const bool in = base + j * STREAM_THREADS + tx < b;
+                const BinAcc r = bin_decode(v[j], in, key, kb, g, f, filtering, n_words, fit);
+                const unsigned m = __match_any_sync(0xFFFFFFFFu, r.act ? r.seg : 0xFFFFFFFFu);
+                pos[j] = 0;
+                if (r.act && lane == (unsigned)(__ffs(m) - 1)) {
+                    unsigned* c = cluster.map_shared_rank(&S.cur[r.seg / CL], r.seg % CL);
+                    pos[j] = atomicAdd(c, (unsigned)__popc(m));
+                }
+                rec[j] = make_uint2(r.rec.x, r.rec.y | (gw << 24));  // the wave rides along (W <= 256)
+                grp[j] = m;
+                act[j] = r.act;
+            }
+#pragma unroll
+            for (unsigned j = 0; j < SCATTER_R; ++j) {
+                const unsigned p = __shfl_sync(0xFFFFFFFFu, pos[j], __ffs(grp[j]) - 1);
+                if (act[j]) w.bin.out[p + __popc(grp[j] & ((1u << lane) - 1u))] = rec[j];
+            }
+        }
+        cluster.sync();  // every add is done before the cursors are reloaded (or the CTAs exit)
+    }
+}
+
+// ------------------------------------------------------------ 5. segments
+//
+// One CTA of 256 threads per segment.  The shadow and the staged accesses come
+// in with cp.async (global -> shared, no register round trip); each wave's
+// accesses are applied with a shared-memory CAS per access and a block barrier
+// between waves; races are buffered in shared memory and appended to the ring
+// with one reservation per segment.
+
+constexpr unsigned SEG_THREADS = 256;
+constexpr unsigned SEG_RACES = 128;  // races a segment buffers (more go to the ring one by one)
+
+struct SegSmem {
+    unsigned long long sh[HR_BIN_SEG];  // the segment's shadow, 8-byte layout
+    uint2 rec[HR_BIN_CHUNK];            // staged accesses (first the compact shadow, if any)
+    unsigned end[HR_BIN_MAX_WAVES];     // bucket ends of this segment
+    unsigned bcwc[HR_BIN_MAX_WAVES];    // wave clocks
+    unsigned kern[HR_BIN_MAX_WAVES];    // rebased kernel ordinals
+    unsigned char clr[HR_BIN_MAX_WAVES];
+    unsigned red[3][SEG_THREADS / 32];
+    unsigned r0, n_races;
+    unsigned long long race_base;
+    hr_race races[SEG_RACES];           // this segment's races, appended to the ring once at the end
+};
+constexpr size_t SEG_SMEM = sizeof(SegSmem);
+static_assert(HR_BIN_CHUNK * sizeof(uint2) >= HR_BIN_SEG * 4, "the compact shadow is staged in the access area");
+
+
+__global__ void __launch_bounds__(SEG_THREADS, 4)
+    hr_bin_segments(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegSmem& S = *reinterpret_cast<SegSmem*>(smem_raw);
+    if (!w.ctl->binned) return;
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev* rg = regions + jb.region;
+    if (*(volatile unsigned*)&rg->error) return;
+    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
+    const unsigned seg = blockIdx.x, tx = threadIdx.x;
+    // this segment's accesses: [row[0], the next row's first entry); a wave's
+    // accesses end where the next wave's first part begins
+    const unsigned* row = w.bin.table + (size_t)seg * P;
+    const unsigned r_end = seg + 1 < w.bin.n_seg ? row[P] : w.ctl->bin_total;
+    for (unsigned p = tx; p < P; p += SEG_THREADS) {
+        const unsigned wv = w.bin.part_wave[p];
+        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.end[wv] = p + 1 == P ? r_end : row[p + 1];
+    }
+    for (unsigned i = tx; i < W; i += SEG_THREADS) {
+        const unsigned long long key = w.wave_key[jb.wave_begin + i];
+        S.bcwc[i] = (unsigned)key;
+        S.kern[i] = (unsigned)(key >> 32);
+        S.clr[i] = w.bin.clear[i];
+    }
+    if (tx == 0) {
+        S.r0 = row[0];
+        S.n_races = 0;
+    }
+    const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
+    const unsigned r0 = S.r0;
+    const unsigned r1 = S.end[W - 1];
+    if (r0 == r1 && !any_clear) return;  // no access and no clear: the segment is untouched
+
+    const hr_geom g = rg->geom;
+    const unsigned long long w0 = (unsigned long long)seg * HR_BIN_SEG;
+    const unsigned nws = (unsigned)min((unsigned long long)HR_BIN_SEG, rg->n_words - w0);
+    unsigned long long* shadow = rg->shadow;
+    const bool compact = g.shadow_bytes == 4;
+    if (r0 == r1) {
+        // only clears: the segment ends cleared
+        for (unsigned i = tx; i < nws; i += SEG_THREADS) {
+            if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = 0u;
+            else shadow[w0 + i] = 0ull;
+        }
+        return;
+    }
+    // the segment's shadow (segment starts are 16-byte aligned; a ragged tail by plain loads)
+    unsigned c0 = r0, c1 = r0;  // staged accesses [c0, c1)
+    if (!compact) {
+        for (unsigned i = tx; i < nws / 2; i += SEG_THREADS) cp_async16(&S.sh[2 * i], shadow + w0 + 2 * i);
+        if ((nws & 1u) && tx == 0) S.sh[nws - 1] = shadow[w0 + nws - 1];
+        c1 = min(r0 + HR_BIN_CHUNK, r1);  // the first accesses come in with it
+        for (unsigned i = c0 + tx; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
+        cp_async_wait_all();
+        __syncthreads();
+    } else {
+        unsigned* raw = reinterpret_cast<unsigned*>(S.rec);
+        const unsigned* src = reinterpret_cast<const unsigned*>(shadow) + w0;
+        for (unsigned i = tx; i < nws / 4; i += SEG_THREADS) cp_async16(&raw[4 * i], src + 4 * i);
+        if (tx < (nws & 3u)) raw[(nws & ~3u) + tx] = src[(nws & ~3u) + tx];
+        cp_async_wait_all();
+        __syncthreads();
+        for (unsigned i = tx; i < nws; i += SEG_THREADS) S.sh[i] = hr_expand32(raw[i], g);
+        __syncthreads();
+    }
+
+    const unsigned cap = w.cas_cap;
+    const unsigned ring_region = rg->region;
+    const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
+    unsigned n_acc = 0, n_cas = 0, n_retry = 0, err = 0;
+    for (unsigned gw = 0; gw < W; ++gw) {
+        if (S.clr[gw]) {  // kernel-tag group change before this wave: the shadow starts over
+            for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
+            __syncthreads();
+        }
+        unsigned b0 = gw ? S.end[gw - 1] : r0;
+        const unsigned b1 = S.end[gw];
+        const unsigned bcwc = S.bcwc[gw], kern = S.kern[gw];
+        const unsigned bc = bcwc >> 16, wc = bcwc & 0xFFFFu, ktag = kern & 7u;
+        while (b0 < b1) {
+            if (b0 >= c1) {  // stage the next accesses (every thread is done with the previous ones)
+                c0 = b0;
+                c1 = min(c0 + HR_BIN_CHUNK, r1);
+                for (unsigned i = c0 + tx; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
+                cp_async_wait_all();
+                __syncthreads();
+            }
+            const unsigned e = min(b1, c1);
+            for (unsigned i = b0 + tx; i < e; i += SEG_THREADS) {
+                const uint2 r = S.rec[i - c0];
+                const unsigned wis = r.y & 0xFFFu, op = (r.y >> 16) & 0xFFu, tid = r.x;
+                unsigned long long o = S.sh[wis];
+                unsigned raced = 0, tries = 0;
+                bool done = false;
+                for (;;) {
+                    raced = 0;
+                    const unsigned long long nv = hr_fsm_step(o, tid, op, bc, wc, ktag, g, gtable, &raced);
+                    if (nv == o) {
+                        done = true;
+                        break;
+                    }
+                    ++n_cas;
+                    const unsigned long long seen = atomicCAS(&S.sh[wis], o, nv);
+                    if (seen == o) {
+                        done = true;
+                        break;
+                    }
+                    if (tries == 0) ++n_retry;  // accesses whose first CAS lost
+                    if (tries++ >= cap) break;
+                    o = seen;
+                }
+                ++n_acc;
+                if (!done) {
+                    err = HR_ERR_CONTENTION;
+                } else if (raced) {
+                    // buffered: a returning atomic on the region's race counter would hold
+                    // the whole CTA at the next barrier
+                    const unsigned k = atomicAdd(&S.n_races, 1u);
+                    if (k < SEG_RACES) {
+                        hr_race& x = S.races[k];
+                        x.word = (unsigned)(word_off + wis);
+                        x.tid = tid;
+                        x.kernel = (uint16_t)kern;
+                        x.epoch = (uint16_t)bc;
+                        x.region = (uint16_t)ring_region;
+                        x.op = (uint8_t)op;
+                        x.prior = (uint8_t)(raced - 1u);
+                    } else {
+                        hr_append_race(rg->ring, rg->ring_cap, &rg->n_races, &rg->flags, (unsigned)(word_off + wis),
+                                       tid, kern, bc, ring_region, op, raced - 1u);
+                    }
+                }
+            }
+            __syncthreads();
+            b0 = e;
+        }
+    }
+    // write the segment back
+    for (unsigned i = tx; i < nws; i += SEG_THREADS) {
+        if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = hr_compress64(S.sh[i], g);
+        else shadow[w0 + i] = S.sh[i];
+    }
+    if (err) hr_set_error(&rg->error, err);
+    // the buffered races: one reservation on the region's counter
+    const unsigned nr = min(S.n_races, SEG_RACES);
+    if (nr) {
+        if (tx == 0) S.race_base = atomicAdd(&rg->n_races, (unsigned long long)nr);
+        __syncthreads();
+        for (unsigned i = tx; i < nr; i += SEG_THREADS) {
+            const unsigned long long slot = S.race_base + i;
+            if (slot < rg->ring_cap) rg->ring[slot] = S.races[i];
+            else atomicOr(&rg->flags, HR_FLAG_TRUNCATED);
+        }
+    }
+    // diagnostics: accesses, CAS attempts, retries
+    const unsigned lane = tx & 31, wid = tx >> 5;
+    unsigned c[3] = {n_acc, n_cas, n_retry};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xFFFFFFFFu, c[k], o);
+        if (lane == 0) S.red[k][wid] = c[k];
+    }
+    __syncthreads();
+    if (tx < 3) {
+        unsigned long long t = 0;
+        for (unsigned i = 0; i < SEG_THREADS / 32; ++i) t += S.red[tx][i];
+        if (t) atomicAdd(&rg->counters[tx], t);
+    }
+}
+
+bool g_attrs = false;
+
+}  // namespace
+
+cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const unsigned char* d_table,
+                             cudaStream_t stream)
+{
+    if (!g_attrs) {
+        // the shared-memory carveout at its maximum: 4 segment CTAs per SM
+        for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_segments})
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(hr_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STREAM_SMEM);
+        cudaFuncSetAttribute(hr_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
+        cudaFuncSetAttribute(hr_bin_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
+        g_attrs = true;
+    }
+    const hr_bin& b = w.bin;
+    if (b.n_seg == 0 || b.n_seg > b.seg_cap || b.n_seg > HR_BIN_MAX_SEGS || b.clusters == 0 || b.sub == 0 ||
+        b.sub > HR_BIN_MAX_SUB || b.slices != b.clusters * b.sub || b.slices > STREAM_THREADS ||
+        b.part_cap < HR_BIN_MAX_WAVES + b.slices - 1)
+        return cudaErrorInvalidValue;
+    const unsigned scan_blocks = (unsigned)(((unsigned long long)b.n_seg * b.part_cap + HR_BIN_SCAN - 1) / HR_BIN_SCAN);
+    hr_bin_count<<<b.slices, STREAM_THREADS, STREAM_SMEM, stream>>>(d_regions, w);
+    hr_bin_scan_sums<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
+    hr_bin_scan<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
+    hr_bin_scatter<<<b.clusters * CL, STREAM_THREADS, SCATTER_SMEM, stream>>>(d_regions, w);
+    hr_bin_segments<<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+    return cudaGetLastError();
+}
+
+// The binned checker's streaming shape: scatter clusters of HR_BIN_CLUSTER CTAs,
+// as many as can be resident at once (one CTA per SM), and count slices per
+// cluster slice so that the count pass (one CTA per SM) fills the SMs.
+void hr_bin_shape(unsigned* clusters_out, unsigned* sub_out)
+{
+    static unsigned c_cached = 0, s_cached = 0;
+    if (!c_cached) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < (int)CL) sms = CL;
+        cudaFuncSetAttribute(hr_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms / CL * CL));
+        cfg.blockDim = dim3(STREAM_THREADS);
+        cfg.dynamicSmemBytes = SCATTER_SMEM;
+        cudaLaunchAttribute attr;
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = CL;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, (void*)hr_bin_scatter, &cfg) != cudaSuccess || clusters < 1) {
+            (void)cudaGetLastError();
+            clusters = sms / (int)CL;
+        }
+        unsigned sub = (unsigned)sms / (unsigned)clusters;
+        if (sub < 1) sub = 1;
+        if (sub > HR_BIN_MAX_SUB) sub = HR_BIN_MAX_SUB;
+        while ((unsigned)clusters * sub > STREAM_THREADS) --sub;
+        c_cached = (unsigned)clusters;
+        s_cached = sub;
+    }
+    *clusters_out = c_cached;
+    *sub_out = s_cached;
+}

@@ -112,8 +112,40 @@ struct hr_ctl {
     unsigned total_items;
     unsigned n_jobs;
     unsigned n_intervals;
-    unsigned pad;
+    unsigned binned;       // 1: the binned checker took this check (the per-wave checker then has no items)
     unsigned long long t0_ns;  // device clock when the check's first kernel started
+    unsigned bin_parts;    // binned checker: (slice, wave) parts of the trace
+    unsigned bin_total;    // binned checker: accesses moved into buckets
+};
+
+// Scratch of the binned checker (hr_binned.cu), one per region.  The region's
+// shadow is cut into segments of HR_BIN_SEG words.  The trace is cut into one
+// contiguous slice per streaming CTA, and a slice into parts, one per wave it
+// meets; parts are numbered in trace order, so their waves ascend.  The table
+// holds, for segment s and part p at s * n_parts + p, first the part's number
+// of accesses to the segment, then (after an exclusive scan in that order) where
+// they go in the bucketed access array: segment-major, waves ascending.
+constexpr unsigned HR_BIN_SEG_SHIFT = 12;
+constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per segment (32 KB in shared memory)
+constexpr unsigned HR_BIN_MAX_SEGS = 16384;              // larger regions take the per-wave checker
+constexpr unsigned HR_BIN_MAX_WAVES = 256;               // checks with more waves take the per-wave checker
+constexpr unsigned HR_BIN_CHUNK = 2048;                  // bucketed accesses staged in shared memory at a time
+constexpr unsigned HR_BIN_SCAN = 4096;                   // table entries per scan block
+constexpr unsigned HR_BIN_CLUSTER = 8;                   // CTAs sharing bucket cursors in the scatter
+constexpr unsigned HR_BIN_MAX_SUB = 16;                  // count slices per cluster slice, at most
+struct hr_bin {
+    unsigned* table;         // [seg_cap * part_cap] counts, then offsets
+    unsigned* sums;          // [seg_cap * part_cap / HR_BIN_SCAN + 1] per scan block
+    unsigned* part_wave;     // [part_cap] wave of each part (ascending)
+    unsigned char* clear;    // [HR_BIN_MAX_WAVES] 1: the shadow is cleared before this wave
+    uint2* out;              // [out_cap] bucketed accesses {tid, op << 16 | word within the segment}
+    unsigned long long out_cap;
+    unsigned n_seg;          // segments of this check's region
+    unsigned seg_cap;        // segments the table holds
+    unsigned part_cap;       // parts the table holds: HR_BIN_MAX_WAVES + slices - 1
+    unsigned clusters;       // scatter clusters (hr_bin_shape())
+    unsigned sub;            // count slices per cluster slice
+    unsigned slices;         // count slices (CTAs of the count pass): clusters * sub
 };
 
 // Scratch of one check (device memory): job table, pre-pass counts, wave
@@ -134,6 +166,7 @@ struct hr_work {
     unsigned cas_cap;                // CAS retries before HR_ERR_CONTENTION
     unsigned long long wait_ns;      // bound of every device-side wait
     unsigned test_flags;             // HR_TEST_* hooks (tests only)
+    hr_bin bin;                      // binned checker scratch (variant HR_BIN_VARIANT only)
 };
 
 constexpr unsigned long long HR_DEFAULT_WAIT_NS = 4000000000ull;  // 4 s
@@ -186,17 +219,25 @@ struct hr_variant {
     int consumers;   // consumer warps per CTA (plus one producer warp)
 };
 constexpr hr_variant HR_VARIANTS[] = {{1, 4, 8}, {0, 4, 8}, {1, 2, 8}, {0, 2, 8}, {1, 8, 4}, {0, 8, 4}};
-constexpr unsigned HR_N_VARIANTS = sizeof(HR_VARIANTS) / sizeof(HR_VARIANTS[0]);
+constexpr unsigned HR_N_SHAPES = sizeof(HR_VARIANTS) / sizeof(HR_VARIANTS[0]);
+// The binned checker (hr_binned.cu): single-trace checks of first-race regions
+// only; batches, and checks it cannot take, run the per-wave checker of shape 3.
+constexpr unsigned HR_BIN_VARIANT = HR_N_SHAPES;
+constexpr unsigned HR_BIN_FALLBACK = 3;
+constexpr unsigned HR_N_VARIANTS = HR_N_SHAPES + 1;  // ids a caller may choose
 // Internal id of the checker that also carries the every-epoch path (shape of
 // variant 3); checks on regions in that report mode use it.
 constexpr unsigned HR_EVERY_EPOCH_VARIANT = HR_N_VARIANTS;
 constexpr unsigned hr_variant_consumers(unsigned v)
 {
-    return v == HR_EVERY_EPOCH_VARIANT ? 8u : (unsigned)HR_VARIANTS[v].consumers;
+    return v == HR_EVERY_EPOCH_VARIANT ? 8u
+                                       : (unsigned)HR_VARIANTS[v == HR_BIN_VARIANT ? HR_BIN_FALLBACK : v].consumers;
 }
 constexpr unsigned hr_variant_tile(unsigned v)
 {
-    return v == HR_EVERY_EPOCH_VARIANT ? 8u * 32u * 2u : HR_VARIANTS[v].consumers * 32u * HR_VARIANTS[v].rpl;
+    return v == HR_EVERY_EPOCH_VARIANT ? 8u * 32u * 2u
+           : v == HR_BIN_VARIANT       ? hr_variant_tile(HR_BIN_FALLBACK)
+                                       : HR_VARIANTS[v].consumers * 32u * HR_VARIANTS[v].rpl;
 }
 #ifndef HR_RING_DEPTH
 #define HR_RING_DEPTH 2
@@ -229,6 +270,21 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_
 void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int);
 int hr_check_grid_size(unsigned variant);
 constexpr unsigned HR_SMALL_INTERVALS = 4096;  // single traces of at most this many pre-pass intervals take the one-CTA pre-pass
+// The binned checker's five launches (hr_binned.cu), queued after the pre-pass
+// of a single-job check; the per-wave checker queued after them finds no items
+// when they took the check.
+cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const unsigned char* d_table,
+                             cudaStream_t stream);
+// The binned checker's streaming shape: as many scatter clusters as fit at once,
+// and count slices per cluster slice so that the count pass fills the SMs.
+void hr_bin_shape(unsigned* clusters, unsigned* sub);
+// bytes of a region's binned-checker tables (without the access buffer)
+inline size_t hr_bin_table_bytes(unsigned seg_cap, unsigned part_cap)
+{
+    auto a = [](size_t x) { return (x + 255) & ~size_t(255); };
+    const size_t e = (size_t)seg_cap * part_cap;
+    return a(e * 4) + a((e / HR_BIN_SCAN + 1) * 4) + a((size_t)part_cap * 4) + a(HR_BIN_MAX_WAVES);
+}
 cudaError_t hr_launch_sync_kernel(hr_region_dev* d_region, cudaStream_t stream);
 cudaError_t hr_launch_reset(hr_region_dev* d_region, unsigned long long* shadow, unsigned long long shadow_bytes,
                             cudaStream_t stream);

@@ -180,6 +180,7 @@ __device__ void scan_counts_body(hr_work& w, unsigned total_int, hr_region_dev* 
         w.ctl->abort = 0;
         w.ctl->total_items = 0;
         w.ctl->n_stages = 0;
+        w.ctl->binned = 0;
         w.ctl->n_waves = over ? 0u : (unsigned)total;
     }
 }
@@ -693,7 +694,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
                               uint64_t* s_empty)
 {
     const uint64_t pol = policy_evict_first();
-    const unsigned total = w.ctl->total_items;
+    const unsigned total = w.ctl->binned ? 0u : w.ctl->total_items;  // binned: the work is done already
     unsigned s = 0, s_begin = 0, s_end = 0, type = 0, dep = HR_NO_DEP, dep_need = 0, region = 0, last = 0;
     unsigned long long w_start = 0, w_end = 0, key = 0, kb = 0;
     const hr_record* trace = nullptr;
@@ -1169,6 +1170,7 @@ void launch_variant(int grid, hr_region_dev* d_regions, const hr_work& w, const 
 int hr_check_grid_size(unsigned variant)
 {
     if (variant > HR_EVERY_EPOCH_VARIANT) variant = 0;
+    if (variant == HR_BIN_VARIANT) variant = HR_BIN_FALLBACK;
     int& cached = g_grid[variant];
     if (cached) return cached;
     switch (variant) {
@@ -1208,6 +1210,9 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
                            cudaEvent_t before_check, unsigned* launches)
 {
     if (variant > HR_EVERY_EPOCH_VARIANT) return cudaErrorInvalidValue;
+    const bool binned = variant == HR_BIN_VARIANT;
+    if (binned && (n_jobs != 1 || !w_in.bin.table)) return cudaErrorInvalidValue;
+    if (binned) variant = HR_BIN_FALLBACK;  // the per-wave checker runs after it (and finds no work when binned)
     hr_work w = w_in;
     w.tile = hr_variant_tile(variant);
     w.consumers = hr_variant_consumers(variant);
@@ -1233,7 +1238,11 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
         launch_prepass(P, total_int, d_regions, w, stream);
     }
     if (before_check) cudaEventRecord(before_check, stream);
-    if (launches) *launches = prepass_launches + 1;
+    if (launches) *launches = prepass_launches + 1 + (binned ? 5 : 0);
+    if (binned) {
+        const cudaError_t e = hr_launch_binned(d_regions, w, d_table, stream);
+        if (e != cudaSuccess) return e;
+    }
     switch (variant) {
     case 0: launch_variant<true, 4, 8>(grid, d_regions, w, d_table, stream); break;
     case 1: launch_variant<false, 4, 8>(grid, d_regions, w, d_table, stream); break;

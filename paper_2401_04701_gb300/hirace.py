@@ -145,14 +145,21 @@ def fsm_table():
 
 
 def variants():
-    """[(id, dict(aggregate, records_per_lane, consumer_warps))] of the checker kernel."""
+    """[(id, dict(aggregate, records_per_lane, consumer_warps, binned))] of the checker: the
+    per-wave kernel's shapes, and the binned checker (reported with zero lanes and warps)."""
     lib = load_library()
     out = []
     for i in range(lib.hr_variant_count()):
         a, r, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
         lib.hr_variant_desc(i, ctypes.byref(a), ctypes.byref(r), ctypes.byref(c))
-        out.append((i, dict(aggregate=bool(a.value), records_per_lane=r.value, consumer_warps=c.value)))
+        out.append((i, dict(aggregate=bool(a.value), records_per_lane=r.value, consumer_warps=c.value,
+                            binned=c.value == 0)))
     return out
+
+
+def binned_variant() -> int:
+    """Variant id of the binned checker (per-segment shadow in shared memory)."""
+    return next(i for i, d in variants() if d["binned"])
 
 
 def state_name(state: int) -> str:
