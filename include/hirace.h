@@ -329,13 +329,15 @@ hr_status hr_destroy(hr_ctx* ctx);
  * the segment, wave by wave.  It takes single-trace checks of regions of at
  * most 2^26 words with at most 256 waves per call; batches, and calls it cannot
  * take, run the per-wave checker of id 3.  Its first check on a region
- * allocates the region's bucket tables (about 400 bytes per segment and SM) and
- * an 8-byte-per-record access buffer, so do that check before capturing calls
- * into a CUDA graph.  Its shared-memory CAS loops are bounded by the same cap.  hr_autotune checks the given trace on `region` with
+ * allocates the region's bucket tables (4 bytes per segment for each of 256
+ * waves plus about one count slice per SM) and an access buffer of 8 bytes per
+ * record, so make that check before capturing calls into a CUDA graph.  Its shared-memory CAS loops are bounded by the same cap.  hr_autotune checks the given trace on `region` with
  * every variant (reset before each run, a warm-up then a timed run on
  * `stream`, synchronous), keeps the fastest for this context's later checks,
  * writes it to *best and the per-variant milliseconds to ms[0..ms_cap), and
- * leaves the region reset.  Returns the region's error if the trace is bad.
+ * leaves the region reset.  A variant whose run ends with HR_ERR_CONTENTION or
+ * HR_ERR_TIMEOUT (a bound of that variant ran out) is skipped and gets -1 ms;
+ * any other error is the trace's, and hr_autotune returns it.
  * Regions in HR_REPORT_EVERY_EPOCH mode always use a checker of their own
  * (variant 3's shape): the variant setting does not apply to them, and
  * hr_autotune on such a region returns HR_ERR_INVALID.

@@ -687,6 +687,7 @@ extern "C" hr_status hr_autotune(hr_ctx* ctx, uint32_t region, const hr_record* 
     ctx->profile = false;
     float best_ms = 0.0f;
     unsigned best_v = saved;
+    bool have_best = false;
     hr_status st = HR_OK;
     for (unsigned v = 0; v < HR_N_VARIANTS && e == cudaSuccess && st == HR_OK; ++v) {
         ctx->variant = v;
@@ -701,11 +702,22 @@ extern "C" hr_status hr_autotune(hr_ctx* ctx, uint32_t region, const hr_record* 
         }
         hr_region_dev h;
         if (st == HR_OK && e == cudaSuccess) st = fetch_region(ctx, region, &h);
-        if (st == HR_OK && h.error != 0) st = (hr_status)h.error;  // the trace itself is bad
+        bool usable = true;
+        if (st == HR_OK && h.error != 0) {
+            // a bounded retry or wait that ran out belongs to this variant: skip it;
+            // any other error is the trace's own
+            if (h.error == HR_ERR_CONTENTION || h.error == HR_ERR_TIMEOUT) {
+                usable = false;
+                t = -1.0f;
+            } else {
+                st = (hr_status)h.error;
+            }
+        }
         if (v < ms_cap) ms[v] = t;
-        if (st == HR_OK && e == cudaSuccess && (v == 0 || t < best_ms)) {
+        if (st == HR_OK && e == cudaSuccess && usable && (!have_best || t < best_ms)) {
             best_ms = t;
             best_v = v;
+            have_best = true;
         }
     }
     ctx->profile = saved_profile;
