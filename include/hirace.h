@@ -421,8 +421,8 @@ hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n, uint64_t*
 const char* hr_status_str(hr_status s);
 
 /*
- * The FSM as a flat table (Sec. IV-B: "encoded as a flat array indexed by a
- * concatenation of oState and the transition labels"): entry
+ * The FSM as a flat table (Sec. IV-B stores it as one array whose index
+ * joins the old state and the transition label bits): entry
  * (oState << 6) | (access << 4) | (tRel << 2) | sRel gives the next state in
  * bits 0..4 and its scope level in bits 5..7 (0xFF marks unused labels).
  * access: 0 R, 1 W, 2 A.  tRel: 0 same thread, 1 same warp, 2 same block,

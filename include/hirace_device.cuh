@@ -182,6 +182,42 @@ static __device__ __forceinline__ uint64_t hr_fsm_step(uint64_t o, uint32_t tid,
     return n;
 }
 
+/* hr_fsm_step for a power-of-two geometry (g.bd_shift != ~0u; bd_shift and
+ * ws_shift are g.bd_shift and g.ws_shift): the same transition, with
+ * compareTids and the scope heads reduced to bit operations on the two tids
+ * and the new value assembled from its two 32-bit halves.  Two tids in one
+ * block (their xor below 2^bd_shift) share a warp when the xor is also below
+ * 2^ws_shift; a warp's first tid clears the low min(ws_shift, bd_shift) bits,
+ * a block's the low bd_shift bits. */
+static __device__ __forceinline__ uint64_t hr_fsm_step_pow2(uint64_t o, uint32_t tid, uint32_t op, uint32_t bc,
+                                                            uint32_t wc, uint32_t ktag, uint32_t bd_shift,
+                                                            uint32_t ws_shift, const unsigned char* table,
+                                                            uint32_t* raced)
+{
+    const uint32_t ohi = (uint32_t)(o >> 32);
+    uint32_t os = ohi >> (HR_SH_STATE_SHIFT - 32);
+    if (os != HR_STATE_INIT && ((ohi >> (HR_SH_KTAG_SHIFT - 32)) & 7u) != ktag) os = HR_STATE_INIT;
+    const uint32_t x = tid ^ (uint32_t)o;
+    const uint32_t trel = x == 0u ? HR_TREL_SAME
+                        : (x >> bd_shift) ? HR_TREL_GRID
+                        : (x >> ws_shift) ? HR_TREL_BLOCK : HR_TREL_WARP;
+    const uint32_t obc = (ohi >> (HR_SH_BC_SHIFT - 32)) & 0xFFFFu;
+    const uint32_t owc = (ohi >> (HR_SH_WC_SHIFT - 32)) & 0xFFu;
+    const uint32_t srel = bc != obc ? HR_SREL_BLOCK : (wc != owc ? HR_SREL_WARP : HR_SREL_UNSYNC);
+    const uint32_t e = table[(os << 6) | (op << 4) | (trel << 2) | srel];
+    const uint32_t ns = e & 31u;
+    const uint32_t lvl = e >> 5;
+    uint32_t hi = (ns << (HR_SH_STATE_SHIFT - 32)) | (ktag << (HR_SH_KTAG_SHIFT - 32));
+    uint32_t lo = 0u;
+    if (lvl >= HR_LVL_THREAD && lvl <= HR_LVL_BLOCK) {
+        const uint32_t low = lvl == HR_LVL_THREAD ? 0u : (lvl == HR_LVL_WARP ? min(ws_shift, bd_shift) : bd_shift);
+        lo = tid & ~((1u << low) - 1u);
+        hi |= (bc << (HR_SH_BC_SHIFT - 32)) | (lvl == HR_LVL_BLOCK ? 0u : (wc << (HR_SH_WC_SHIFT - 32)));
+    }
+    if (ns == HR_STATE_RACE && os != HR_STATE_RACE) *raced = 1u + os;
+    return ((uint64_t)hi << 32) | lo;
+}
+
 static __device__ __forceinline__ uint64_t hr_ld_relaxed(const unsigned long long* p)
 {
     uint64_t v;

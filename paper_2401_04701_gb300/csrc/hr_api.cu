@@ -289,6 +289,7 @@ static hr_status ensure_bin(RegionHost& r, uint64_t n, cudaStream_t s)
         r.bin.out_cap = n;
     }
     r.bin.n_seg = n_seg;
+    r.bin.pow2 = hr_desc_geom(r.desc).bd_shift != ~0u ? 1u : 0u;
     return HR_OK;
 }
 

@@ -494,26 +494,36 @@ __global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_
 // between waves; races are buffered in shared memory and appended to the ring
 // with one reservation per segment.
 
-constexpr unsigned SEG_THREADS = 256;
+#ifndef HR_BIN_SEG_THREADS
+#define HR_BIN_SEG_THREADS 256
+#endif
+#ifndef HR_BIN_SEG_MIN_CTAS
+#define HR_BIN_SEG_MIN_CTAS 4
+#endif
+constexpr unsigned SEG_THREADS = HR_BIN_SEG_THREADS;
 constexpr unsigned SEG_RACES = 128;  // races a segment buffers (more go to the ring one by one)
 
 struct SegSmem {
     unsigned long long sh[HR_BIN_SEG];  // the segment's shadow, 8-byte layout
     uint2 rec[HR_BIN_CHUNK];            // staged accesses (first the compact shadow, if any)
-    unsigned end[HR_BIN_MAX_WAVES];     // bucket ends of this segment
-    unsigned bcwc[HR_BIN_MAX_WAVES];    // wave clocks
+    uint2 wave[HR_BIN_MAX_WAVES];       // per wave: end of the segment's bucket, bc << 16 | wc
     unsigned kern[HR_BIN_MAX_WAVES];    // rebased kernel ordinals
     unsigned char clr[HR_BIN_MAX_WAVES];
+    unsigned char tab[2048];            // the FSM table
     unsigned red[3][SEG_THREADS / 32];
     unsigned r0, n_races;
     unsigned long long race_base;
     hr_race races[SEG_RACES];           // this segment's races, appended to the ring once at the end
 };
 constexpr size_t SEG_SMEM = sizeof(SegSmem);
+static_assert((SEG_SMEM + 1024) * HR_BIN_SEG_MIN_CTAS <= 228 * 1024, "the segment CTAs of one SM fit its shared memory");
 static_assert(HR_BIN_CHUNK * sizeof(uint2) >= HR_BIN_SEG * 4, "the compact shadow is staged in the access area");
 
 
-__global__ void __launch_bounds__(SEG_THREADS, 4)
+// POW2: the region's block size and warp size are powers of two (hr_bin::pow2),
+// and the FSM step takes its bit-operation form
+template <bool POW2>
+__global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
     hr_bin_segments(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -530,21 +540,23 @@ __global__ void __launch_bounds__(SEG_THREADS, 4)
     const unsigned r_end = seg + 1 < w.bin.n_seg ? row[P] : w.ctl->bin_total;
     for (unsigned p = tx; p < P; p += SEG_THREADS) {
         const unsigned wv = w.bin.part_wave[p];
-        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.end[wv] = p + 1 == P ? r_end : row[p + 1];
+        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.wave[wv].x = p + 1 == P ? r_end : row[p + 1];
     }
     for (unsigned i = tx; i < W; i += SEG_THREADS) {
         const unsigned long long key = w.wave_key[jb.wave_begin + i];
-        S.bcwc[i] = (unsigned)key;
+        S.wave[i].y = (unsigned)key;
         S.kern[i] = (unsigned)(key >> 32);
         S.clr[i] = w.bin.clear[i];
     }
+    for (unsigned i = tx; i < 2048 / 4; i += SEG_THREADS)
+        reinterpret_cast<unsigned*>(S.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
     if (tx == 0) {
         S.r0 = row[0];
         S.n_races = 0;
     }
     const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
     const unsigned r0 = S.r0;
-    const unsigned r1 = S.end[W - 1];
+    const unsigned r1 = S.wave[W - 1].x;
     if (r0 == r1 && !any_clear) return;  // no access and no clear: the segment is untouched
 
     const hr_geom g = rg->geom;
@@ -584,14 +596,15 @@ __global__ void __launch_bounds__(SEG_THREADS, 4)
     const unsigned ring_region = rg->region;
     const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
     unsigned n_acc = 0, n_cas = 0, n_retry = 0, err = 0;
+    unsigned b0 = r0;  // the wave's bucket starts where the previous one ended
     for (unsigned gw = 0; gw < W; ++gw) {
+        const uint2 wv = S.wave[gw];
         if (S.clr[gw]) {  // kernel-tag group change before this wave: the shadow starts over
             for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
             __syncthreads();
         }
-        unsigned b0 = gw ? S.end[gw - 1] : r0;
-        const unsigned b1 = S.end[gw];
-        const unsigned bcwc = S.bcwc[gw], kern = S.kern[gw];
+        const unsigned b1 = wv.x;
+        const unsigned bcwc = wv.y, kern = S.kern[gw];
         const unsigned bc = bcwc >> 16, wc = bcwc & 0xFFFFu, ktag = kern & 7u;
         while (b0 < b1) {
             if (b0 >= c1) {  // stage the next accesses (every thread is done with the previous ones)
@@ -604,13 +617,15 @@ __global__ void __launch_bounds__(SEG_THREADS, 4)
             const unsigned e = min(b1, c1);
             for (unsigned i = b0 + tx; i < e; i += SEG_THREADS) {
                 const uint2 r = S.rec[i - c0];
-                const unsigned wis = r.y & 0xFFFu, op = (r.y >> 16) & 0xFFu, tid = r.x;
+                const unsigned wis = r.y & (HR_BIN_SEG - 1u), op = (r.y >> 16) & 0xFFu, tid = r.x;
                 unsigned long long o = S.sh[wis];
                 unsigned raced = 0, tries = 0;
                 bool done = false;
                 for (;;) {
                     raced = 0;
-                    const unsigned long long nv = hr_fsm_step(o, tid, op, bc, wc, ktag, g, gtable, &raced);
+                    const unsigned long long nv =
+                        POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab, &raced)
+                             : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
                     if (nv == o) {
                         done = true;
                         break;
@@ -693,11 +708,13 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
 {
     if (!g_attrs) {
         // the shared-memory carveout at its maximum: 4 segment CTAs per SM
-        for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_segments})
+        for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_segments<true>,
+                              (const void*)hr_bin_segments<false>})
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(hr_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STREAM_SMEM);
         cudaFuncSetAttribute(hr_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
-        cudaFuncSetAttribute(hr_bin_segments, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
+        cudaFuncSetAttribute(hr_bin_segments<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
+        cudaFuncSetAttribute(hr_bin_segments<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
         g_attrs = true;
     }
     const hr_bin& b = w.bin;
@@ -710,7 +727,8 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
     hr_bin_scan_sums<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scan<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scatter<<<b.clusters * CL, STREAM_THREADS, SCATTER_SMEM, stream>>>(d_regions, w);
-    hr_bin_segments<<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+    if (b.pow2) hr_bin_segments<true><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+    else hr_bin_segments<false><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
     return cudaGetLastError();
 }
 

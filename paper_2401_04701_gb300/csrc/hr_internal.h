@@ -125,11 +125,15 @@ struct hr_ctl {
 // holds, for segment s and part p at s * n_parts + p, first the part's number
 // of accesses to the segment, then (after an exclusive scan in that order) where
 // they go in the bucketed access array: segment-major, waves ascending.
-constexpr unsigned HR_BIN_SEG_SHIFT = 12;
-constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per segment (32 KB in shared memory)
+#ifndef HR_BIN_SEG_SHIFT_BITS
+#define HR_BIN_SEG_SHIFT_BITS 12
+#endif
+constexpr unsigned HR_BIN_SEG_SHIFT = HR_BIN_SEG_SHIFT_BITS;
+constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per segment (8 B each in shared memory)
+static_assert(HR_BIN_SEG_SHIFT >= 10 && HR_BIN_SEG_SHIFT <= 13, "the packed access keeps 16 bits for the word");
 constexpr unsigned HR_BIN_MAX_SEGS = 16384;              // larger regions take the per-wave checker
 constexpr unsigned HR_BIN_MAX_WAVES = 256;               // checks with more waves take the per-wave checker
-constexpr unsigned HR_BIN_CHUNK = 2048;                  // bucketed accesses staged in shared memory at a time
+constexpr unsigned HR_BIN_CHUNK = HR_BIN_SEG / 2;        // bucketed accesses staged in shared memory at a time
 constexpr unsigned HR_BIN_SCAN = 4096;                   // table entries per scan block
 constexpr unsigned HR_BIN_CLUSTER = 8;                   // CTAs sharing bucket cursors in the scatter
 constexpr unsigned HR_BIN_MAX_SUB = 16;                  // count slices per cluster slice, at most
@@ -146,6 +150,7 @@ struct hr_bin {
     unsigned clusters;       // scatter clusters (hr_bin_shape())
     unsigned sub;            // count slices per cluster slice
     unsigned slices;         // count slices (CTAs of the count pass): clusters * sub
+    unsigned pow2;           // 1: block size and warp size are powers of two (bit-operation FSM step)
 };
 
 // Scratch of one check (device memory): job table, pre-pass counts, wave

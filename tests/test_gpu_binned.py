@@ -102,7 +102,7 @@ def test_random_programs_across_segments(oracle_mod, hr):
     rng = np.random.default_rng(161)
     seen = 0
     for it in range(24):
-        bd = int(rng.choice([3, 40, 64, 256]))
+        bd = int(rng.choice([3, 16, 40, 64, 256]))   # 16 with warp 32: one warp per block
         ws = int(rng.choice([2, 32]))
         n_words = int(rng.choice([16, SEG + 1, 3 * SEG + 5, 20000]))
         kernels = C.random_program(rng, n_threads=int(rng.integers(2, 700)), block_dim=bd, n_words=n_words,
