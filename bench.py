@@ -483,6 +483,39 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def check_latency(ck, d_trace, stream, expect, n):
+    """Latency of one check issued alone: n times, reset the region, then
+    hr_check_trace on an idle stream (device time between CUDA events around
+    it) and hr_report (host time from the check's submission until the race
+    records are on the host).  Runs after the throughput loop, outside its
+    timed region.  p50 / p99 / max in ms."""
+    import torch
+    from paper_2401_04701_gb300 import hirace
+    if n <= 0:
+        return None
+    dev_ms, rep_ms = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(n):
+        ck.reset(0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        ck.check_trace(0, d_trace)
+        e1.record(stream)
+        _, status, n_total, _ = ck.report(0)
+        rep_ms.append((time.perf_counter() - t0) * 1e3)
+        dev_ms.append(e0.elapsed_time(e1))
+        if status != hirace.HR_OK or n_total != expect:
+            raise SystemExit("latency check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
+
+    def q(v):
+        v = np.asarray(v)
+        return {"p50": float(np.percentile(v, 50)), "p99": float(np.percentile(v, 99)), "max": float(v.max())}
+    return {"checks": n, "device_ms": q(dev_ms), "to_report_ms": q(rep_ms),
+            "what": "one check of the whole trace issued alone after a reset: device time of hr_check_trace, "
+                    "and host time from its submission until hr_report returned the race records"}
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     from paper_2401_04701_gb300 import hirace
@@ -571,6 +604,7 @@ def run_gpu(args, rank, world, local_rank):
             raise SystemExit("end-to-end check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
     e2e_s = time.perf_counter() - t0
     e2e_rate = world * n_acc * e2e_steps / e2e_s if e2e_steps else None
+    latency = check_latency(ck, d_trace, stream, expect, args.latency_checks) if default else None
 
     if rank != 0:
         ck.close()
@@ -619,6 +653,8 @@ def run_gpu(args, rank, world, local_rank):
                      "ms_per_variant": [round(t, 4) for t in tune_ms] if tune_ms else "pinned by --variant"},
         "clocks": clk,
     }
+    if latency:
+        line["check_latency"] = latency
     if cpu:
         line["cpu_baseline"] = cpu
     if default and not args.no_mode_lines:
@@ -650,6 +686,8 @@ def main():
                     help="random 8-byte load/CAS/store rates over 16..512 MB arrays, then exit")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
+    ap.add_argument("--latency-checks", type=int, default=50,
+                    help="single checks timed one at a time for the p50/p99 check latency (default workload)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the checker kernel variant instead of autotuning")
     ap.add_argument("--no-mode-lines", action="store_true",
