@@ -595,7 +595,8 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
     const unsigned cap = w.cas_cap;
     const unsigned ring_region = rg->region;
     const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
-    unsigned n_acc = 0, n_cas = 0, n_retry = 0, err = 0;
+    unsigned n_cas = 0, n_retry = 0, err = 0;
+    const unsigned n_acc = tx == 0 ? r1 - r0 : 0u;  // every access of [r0, r1) is applied once
     unsigned b0 = r0;  // the wave's bucket starts where the previous one ended
     for (unsigned gw = 0; gw < W; ++gw) {
         const uint2 wv = S.wave[gw];
@@ -619,28 +620,38 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
                 const uint2 r = S.rec[i - c0];
                 const unsigned wis = r.y & (HR_BIN_SEG - 1u), op = (r.y >> 16) & 0xFFu, tid = r.x;
                 unsigned long long o = S.sh[wis];
-                unsigned raced = 0, tries = 0;
-                bool done = false;
-                for (;;) {
-                    raced = 0;
-                    const unsigned long long nv =
-                        POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab, &raced)
-                             : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
-                    if (nv == o) {
-                        done = true;
-                        break;
-                    }
+                unsigned raced = 0;
+                unsigned long long nv =
+                    POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab, &raced)
+                         : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
+                bool done = true;
+                if (nv != o) {
                     ++n_cas;
-                    const unsigned long long seen = atomicCAS(&S.sh[wis], o, nv);
-                    if (seen == o) {
-                        done = true;
-                        break;
+                    unsigned long long seen = atomicCAS(&S.sh[wis], o, nv);
+                    if (seen != o) {
+                        // another access of this wave changed the word first: fold into
+                        // what it left, at most cap more times
+                        ++n_retry;
+                        done = false;
+                        for (unsigned tries = 0; tries < cap; ++tries) {
+                            o = seen;
+                            raced = 0;
+                            nv = POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab,
+                                                         &raced)
+                                      : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
+                            if (nv == o) {
+                                done = true;
+                                break;
+                            }
+                            ++n_cas;
+                            seen = atomicCAS(&S.sh[wis], o, nv);
+                            if (seen == o) {
+                                done = true;
+                                break;
+                            }
+                        }
                     }
-                    if (tries == 0) ++n_retry;  // accesses whose first CAS lost
-                    if (tries++ >= cap) break;
-                    o = seen;
                 }
-                ++n_acc;
                 if (!done) {
                     err = HR_ERR_CONTENTION;
                 } else if (raced) {
