@@ -506,9 +506,11 @@ constexpr unsigned SEG_RACES = 128;  // races a segment buffers (more go to the 
 struct SegSmem {
     unsigned long long sh[HR_BIN_SEG];  // the segment's shadow, 8-byte layout
     uint2 rec[HR_BIN_CHUNK];            // staged accesses (first the compact shadow, if any)
-    uint2 wave[HR_BIN_MAX_WAVES];       // per wave: end of the segment's bucket, bc << 16 | wc
-    unsigned kern[HR_BIN_MAX_WAVES];    // rebased kernel ordinals
-    unsigned char clr[HR_BIN_MAX_WAVES];
+    // per wave: x = end of the segment's bucket; y = bc << 16 | clear << 15 | ktag << 8 | wc
+    // (clear: the shadow starts over before the wave; a wave with accesses has wc <= 255,
+    // else the count pass stopped the check with HR_ERR_CLOCK_OVERFLOW)
+    uint2 wave[HR_BIN_MAX_WAVES];
+    unsigned kern[HR_BIN_MAX_WAVES];    // rebased kernel ordinals (race records)
     unsigned char tab[2048];            // the FSM table
     unsigned red[3][SEG_THREADS / 32];
     unsigned r0, n_races;
@@ -544,9 +546,10 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
     }
     for (unsigned i = tx; i < W; i += SEG_THREADS) {
         const unsigned long long key = w.wave_key[jb.wave_begin + i];
-        S.wave[i].y = (unsigned)key;
-        S.kern[i] = (unsigned)(key >> 32);
-        S.clr[i] = w.bin.clear[i];
+        const unsigned kern = (unsigned)(key >> 32);
+        S.wave[i].y = ((unsigned)key & 0xFFFF0000u) | (w.bin.clear[i] ? 0x8000u : 0u) | ((kern & 7u) << 8) |
+                      ((unsigned)key & 0xFFu);
+        S.kern[i] = kern;
     }
     for (unsigned i = tx; i < 2048 / 4; i += SEG_THREADS)
         reinterpret_cast<unsigned*>(S.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
@@ -600,13 +603,12 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
     unsigned b0 = r0;  // the wave's bucket starts where the previous one ended
     for (unsigned gw = 0; gw < W; ++gw) {
         const uint2 wv = S.wave[gw];
-        if (S.clr[gw]) {  // kernel-tag group change before this wave: the shadow starts over
+        if (wv.y & 0x8000u) {  // kernel-tag group change before this wave: the shadow starts over
             for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
             __syncthreads();
         }
         const unsigned b1 = wv.x;
-        const unsigned bcwc = wv.y, kern = S.kern[gw];
-        const unsigned bc = bcwc >> 16, wc = bcwc & 0xFFFFu, ktag = kern & 7u;
+        const unsigned bc = wv.y >> 16, wc = wv.y & 0xFFu, ktag = (wv.y >> 8) & 7u;
         while (b0 < b1) {
             if (b0 >= c1) {  // stage the next accesses (every thread is done with the previous ones)
                 c0 = b0;
@@ -662,14 +664,14 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
                         hr_race& x = S.races[k];
                         x.word = (unsigned)(word_off + wis);
                         x.tid = tid;
-                        x.kernel = (uint16_t)kern;
+                        x.kernel = (uint16_t)S.kern[gw];
                         x.epoch = (uint16_t)bc;
                         x.region = (uint16_t)ring_region;
                         x.op = (uint8_t)op;
                         x.prior = (uint8_t)(raced - 1u);
                     } else {
                         hr_append_race(rg->ring, rg->ring_cap, &rg->n_races, &rg->flags, (unsigned)(word_off + wis),
-                                       tid, kern, bc, ring_region, op, raced - 1u);
+                                       tid, S.kern[gw], bc, ring_region, op, raced - 1u);
                     }
                 }
             }
