@@ -457,27 +457,26 @@ def tg_seed(k):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the CPU oracle as it stands, on the host cores."""
+    """Reference arm: the CPU oracle as it stands, on the host cores, over the
+    whole benchmark trace each step (the same workload the GPU arm checks)."""
     if rank != 0:
         return
     trace, info, n_acc, n_sync = make_workload()
-    # bounded sample: the first block epoch (bc == 0) of the same trace
-    cut = int(np.searchsorted((trace["bc"] > 0).view(np.uint8), 1))
     cores = host_cores()
     for _ in range(args.warmup):
-        cpu_oracle_rate(trace, info, n_acc, max_records=cut, threads=cores)
+        cpu_oracle_rate(trace, info, n_acc, threads=cores)
     tot_acc, tot_t = 0, 0.0
     for _ in range(args.steps):
-        _, dt, acc = cpu_oracle_rate(trace, info, n_acc, max_records=cut, threads=cores)
+        _, dt, acc = cpu_oracle_rate(trace, info, n_acc, threads=cores)
         tot_acc += acc
         tot_t += dt
     value = tot_acc / tot_t
-    sample = ("first block epoch of the workload (%d records, %d accesses), serial FSM oracle on %d word "
-              "ranges, one host thread each" % (cut, tot_acc // args.steps, cores))
+    sample = ("the whole workload each step (%d records, %d accesses): serial FSM oracle in C on %d disjoint word "
+              "ranges, one host thread each" % (len(trace), n_acc, cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "bc==0 epoch"},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "whole trace"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -547,6 +546,7 @@ def run_gpu(args, rank, world, local_rank):
     # here later checks must repeat the first one's count)
     ck.check_trace(0, d_trace)
     races, status, n_total, _ = ck.report(0)
+    gate_races = races
     expect = len(info["injected"]) if args.workload == "global" else n_total
     if status != hirace.HR_OK or n_total != expect:
         raise SystemExit("bench workload check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
@@ -623,12 +623,17 @@ def run_gpu(args, rank, world, local_rank):
         t0 = time.perf_counter()
         bf = oracle.bruteforce_parallel(trace, info["block_dim"], info["n_words"], threads=cores)
         dtb = time.perf_counter() - t0
+        # the GPU's racy (kernel, word, epoch) set of the correctness-gate check
+        # against the brute force on the same trace
+        match = hirace.race_keys(gate_races) == oracle.race_keys(bf)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "whole workload once (%d accesses, %.1f s): serial FSM oracle in C on %d disjoint "
                          "word ranges, one host thread each" % (acc, dt, cores),
                "single_core": {"value": rate1, "cores": 1, "seconds": dt1},
                "bruteforce_all_cores": {"value": n_acc / dtb, "cores": cores, "seconds": dtb,
-                                        "racy_words": int(len(bf))}}
+                                        "racy_words": int(len(bf)), "racy_words_match": bool(match)}}
+        if not match:
+            raise SystemExit("GPU race set differs from the oracle's brute force on the benchmark trace")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -682,8 +687,6 @@ def main():
     ap.add_argument("--all-workloads", action="store_true",
                     help="also time the tree-reduction and power-law workloads (adds ~2 min)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
-    ap.add_argument("--probe-memory", action="store_true",
-                    help="random 8-byte load/CAS/store rates over 16..512 MB arrays, then exit")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
     ap.add_argument("--latency-checks", type=int, default=50,
@@ -705,20 +708,6 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
-        return
-    if args.probe_memory:
-        import torch
-        from paper_2401_04701_gb300 import hirace
-        torch.cuda.set_device(local_rank)
-        dev = torch.device("cuda", local_rank)
-        out = {"random_access_G_ops_per_s": hirace.probe_random_access(dev)}
-        # the benchmark trace's own access pattern, without ordering or state machine
-        trace, info, n_acc, n_sync = make_workload(args.blocks)
-        d_trace = torch.from_numpy(trace.view(np.uint8)).to(dev)
-        out["trace_access_ms"] = {"workload": workload_name(args.blocks, info["n_words"], n_acc, n_sync),
-                                  "accesses": n_acc, "records": len(trace),
-                                  "by_array_size": hirace.probe_trace_access(d_trace)}
-        print(json.dumps(out))
         return
     if args.serving_only:
         import torch

@@ -384,8 +384,14 @@ hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uin
  * on an implicit device synchronisation.  No context is needed and nothing is
  * allocated: no cudaMalloc, cudaFree or allocating library routine is called.
  *   d_trace   n records, device memory, same rules as hr_check_trace
- *   d_shadow  n_words 8-byte shadow values, caller-owned device memory, read
- *             and updated in place; all zero = every word INIT (a fresh region)
+ *   d_shadow  n_words 8-byte shadow values, caller-owned device memory.  Each
+ *             call checks one complete trace as a fresh region: before the
+ *             trace's first wave the call clears d_shadow (every word INIT),
+ *             so what an earlier call or the caller left there does not
+ *             matter, and kernel ordinals are not ordered against an earlier
+ *             call's.  On return it holds the state after the trace.  A trace
+ *             cut into several calls is not continued: use hr_check_trace on a
+ *             context for that.
  *   d_races   race_cap race records (device), written from slot 0
  *   d_result  device hr_result, overwritten: races found by this call (may
  *             exceed race_cap), its sticky error, HR_FLAG_* flags
@@ -397,7 +403,9 @@ hr_status hr_profile_read(hr_ctx* ctx, double* check_ms, double* prepass_ms, uin
  * HR_ERR_CAPACITY and nothing is checked.  The first call on each device
  * looks up the array's device address and copies the FSM table into it with
  * a synchronous cudaMemcpy, so make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
+ * capture.  The address is cached per device for the life of the process, so
+ * a cudaDeviceReset on a device invalidates this entry point there until the
+ * library is reloaded.  All calls share the array and it keeps the last call's contents
  * (each call re-initialises what must start at zero); calls whose work
  * overlaps on the GPU race on it, so serialise them.  Asynchronous on
  * `stream` after the first call.  Returns HR_ERR_INVALID for bad arguments,

@@ -57,7 +57,8 @@ struct hr_region_dev {
     unsigned int error;           // sticky first error (hr_status)
     unsigned int flags;           // HR_FLAG_* bits
     unsigned long long last_key;  // wave key after the region's last processed record
-    unsigned int used;            // any record processed since init/reset
+    unsigned int used;            // 1: a record was processed since init/reset; 2: the shadow's
+                                  // contents are unknown (cleared before the first wave)
     unsigned int region;
     unsigned long long counters[4];  // accesses, CAS attempts, CAS retries, merged lanes
     hr_geom geom;

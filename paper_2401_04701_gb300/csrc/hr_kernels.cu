@@ -236,7 +236,9 @@ __device__ __forceinline__ void wave_plan(const hr_work& w, const hr_jobd& jb, c
     const unsigned g = jb.wave_begin + L;
     const unsigned long long kern = w.wave_key[g] >> 32;
     const unsigned long long prev = L ? (w.wave_key[g - 1] >> 32) : (rg.last_key >> 32);
-    *clear = (L > 0 || rg.used) && (kern >> 3) != (prev >> 3);
+    // used == 2: the region's shadow holds unknown contents (a caller-owned
+    // shadow handed to a one-shot check), so the first wave starts from a clear
+    *clear = (L > 0 || rg.used) && ((kern >> 3) != (prev >> 3) || (L == 0 && rg.used == 2));
     const unsigned long long end = L + 1 < jb.n_waves ? w.wave_start[g + 1] : jb.n;
     w.wave_end[g] = end;
     *rec_items = (unsigned)((end - w.wave_start[g] + w.tile - 1) / w.tile);

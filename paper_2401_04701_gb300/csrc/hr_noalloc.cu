@@ -56,6 +56,9 @@ cudaError_t setup_device(int dev, unsigned char** out)
         uint8_t table[2048];
         hr_fsm_table(table, nullptr);
         e = cudaMemcpy((unsigned char*)p + OFF_TABLE, table, sizeof table, cudaMemcpyHostToDevice);
+        // a copy from pageable memory may return before it lands, and the caller's
+        // stream may be one that does not wait for the legacy stream
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return e;
         g_scratch[dev] = (unsigned char*)p;
     }
@@ -73,8 +76,10 @@ __global__ void hr_noalloc_begin(hr_region_dev* region, unsigned long long* shad
     region->n_races = 0;
     region->error = 0;
     region->flags = 0;
+    // every call is a fresh check: kernel ordinals start over and the shadow is
+    // cleared before the first wave, whatever an earlier call left in it
     region->last_key = 0;
-    region->used = 0;
+    region->used = 2;
     region->region = 0;
     for (int i = 0; i < 4; ++i) region->counters[i] = 0;
     region->geom = geom;

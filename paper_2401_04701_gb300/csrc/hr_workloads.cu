@@ -204,146 +204,3 @@ extern "C" int hrw_smem_reduce(const hr_view* view, int mode, const float* in, f
         smem_reduce_kernel<2><<<grid, block, smem, s>>>(*view, in, out, n, drop_level);
     return cudaGetLastError() == cudaSuccess ? 0 : 3;
 }
-
-// ---------------------------------------------------------------------------
-// Memory-system probe: random 8-byte accesses over an array of 2^lg words.
-// mode 0 relaxed load, 1 CAS, 2 load then CAS, 3 atomicAdd (no return),
-// 4 plain store.  Indices are hash(i) & (2^lg - 1), always in bounds.
-// ---------------------------------------------------------------------------
-namespace {
-
-__device__ __forceinline__ uint32_t probe_hash(uint32_t x)
-{
-    x ^= x >> 16;
-    x *= 0x7feb352dU;
-    x ^= x >> 15;
-    x *= 0x846ca68bU;
-    x ^= x >> 16;
-    return x;
-}
-
-template <int MODE>
-__global__ void probe_kernel(unsigned long long* a, uint32_t mask, uint32_t total, unsigned long long* sink)
-{
-    constexpr int PER = 8;
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t stride = gridDim.x * blockDim.x;
-    unsigned long long acc = 0;
-    for (uint32_t base = i; base < total; base += stride * PER) {
-        uint32_t idx[PER];
-        unsigned long long v[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) idx[k] = probe_hash(base + k * stride) & mask;
-        if (MODE == 0 || MODE == 2) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) v[k] = hr_ld_relaxed(a + idx[k]);
-        }
-        if (MODE == 1) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) v[k] = atomicCAS(a + idx[k], 0ull, (unsigned long long)(base + k));
-        } else if (MODE == 2) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) v[k] = atomicCAS(a + idx[k], v[k], v[k] + 1);
-        } else if (MODE == 3) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) atomicAdd(a + idx[k], 1ull);
-        } else if (MODE == 4) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) a[idx[k]] = base + k;
-        }
-        if (MODE <= 2) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) acc += v[k];
-        }
-    }
-    if (acc == 0x123456789ull) *sink = acc;
-}
-
-}  // namespace
-
-// Launch one probe pass: `total` random accesses over a[0 .. 2^lg).  a must
-// hold at least 2^lg words and sink one word.  Returns 0, 1 for bad arguments.
-extern "C" int hrw_probe(int mode, unsigned long long* a, uint32_t lg, uint32_t total, unsigned long long* sink,
-                         uint32_t grid, uint32_t block, hr_stream_t stream)
-{
-    if (!a || !sink || lg > 31 || mode < 0 || mode > 4 || grid == 0 || block == 0 || block > 1024) return 1;
-    const uint32_t mask = (lg == 32) ? 0xFFFFFFFFu : ((1u << lg) - 1u);
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (mode) {
-    case 0: probe_kernel<0><<<grid, block, 0, s>>>(a, mask, total, sink); break;
-    case 1: probe_kernel<1><<<grid, block, 0, s>>>(a, mask, total, sink); break;
-    case 2: probe_kernel<2><<<grid, block, 0, s>>>(a, mask, total, sink); break;
-    case 3: probe_kernel<3><<<grid, block, 0, s>>>(a, mask, total, sink); break;
-    default: probe_kernel<4><<<grid, block, 0, s>>>(a, mask, total, sink); break;
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : 3;
-}
-
-// ---------------------------------------------------------------------------
-// Trace-driven memory probe: the memory work of a check without its ordering
-// or its state machine.  Every access record (op R, W or A) of a trace touches
-// shadow[word & mask] of an array of 8-byte words; records are taken in a
-// grid-stride order with 4 per thread in flight.  mode 0: load; 1: load then
-// CAS(value, value + 1); 2: atomicAdd without return; 3: records only (the
-// stream).  Indices are masked, always in bounds.
-// ---------------------------------------------------------------------------
-namespace {
-
-template <int MODE>
-__global__ void trace_probe_kernel(const uint4* __restrict__ rec, unsigned long long n, unsigned long long* sh,
-                                   uint32_t mask, unsigned long long* sink)
-{
-    constexpr int PER = 4;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    unsigned long long acc = 0;
-    for (unsigned long long b = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; b < n; b += stride * PER) {
-        uint4 r[PER];
-        bool a[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            const unsigned long long i = b + k * stride;
-            r[k] = i < n ? rec[i] : make_uint4(0, 0, 0, 0xFFFFFFFFu);
-            a[k] = i < n && ((r[k].w >> 16) & 0xFFu) <= 2u;
-        }
-        if (MODE == 3) {
-#pragma unroll
-            for (int k = 0; k < PER; ++k) acc += r[k].x;
-            continue;
-        }
-        unsigned long long v[PER];
-#pragma unroll
-        for (int k = 0; k < PER; ++k) v[k] = (a[k] && MODE != 2) ? hr_ld_relaxed(sh + (r[k].x & mask)) : 0ull;
-#pragma unroll
-        for (int k = 0; k < PER; ++k) {
-            if (!a[k]) continue;
-            if (MODE == 1) v[k] = atomicCAS(sh + (r[k].x & mask), v[k], v[k] + 1);
-            if (MODE == 2) atomicAdd(sh + (r[k].x & mask), 1ull);
-            acc += v[k];
-        }
-    }
-    if (acc == 0x123456789ull) *sink = acc;
-}
-
-}  // namespace
-
-// One trace-probe pass over n records (16-byte, device memory, 16-byte aligned)
-// against sh[0 .. 2^lg).  sh must hold 2^lg words and sink one word.
-// Returns 0, 1 for bad arguments.
-extern "C" int hrw_trace_probe(int mode, const void* records, unsigned long long n, unsigned long long* sh,
-                               uint32_t lg, unsigned long long* sink, uint32_t grid, uint32_t block,
-                               hr_stream_t stream)
-{
-    if (!records || ((uintptr_t)records & 15u) || !sh || !sink || lg > 31 || mode < 0 || mode > 3 || grid == 0 ||
-        block == 0 || block > 1024)
-        return 1;
-    const uint32_t mask = (1u << lg) - 1u;
-    const uint4* r = (const uint4*)records;
-    cudaStream_t s = (cudaStream_t)stream;
-    switch (mode) {
-    case 0: trace_probe_kernel<0><<<grid, block, 0, s>>>(r, n, sh, mask, sink); break;
-    case 1: trace_probe_kernel<1><<<grid, block, 0, s>>>(r, n, sh, mask, sink); break;
-    case 2: trace_probe_kernel<2><<<grid, block, 0, s>>>(r, n, sh, mask, sink); break;
-    default: trace_probe_kernel<3><<<grid, block, 0, s>>>(r, n, sh, mask, sink); break;
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : 3;
-}

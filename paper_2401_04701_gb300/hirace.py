@@ -437,11 +437,8 @@ def load_workloads():
     lib.hrw_stencil.argtypes = [VP, P, P, u32, u32, u32, P]
     lib.hrw_histogram.argtypes = [VP, P, u32, P, u32, u32, P]
     lib.hrw_reduce.argtypes = [VP, P, u32, u32, i32, P]
-    lib.hrw_probe.argtypes = [i32, P, u32, u32, P, u32, u32, P]
-    lib.hrw_trace_probe.argtypes = [i32, P, ctypes.c_uint64, P, u32, P, u32, u32, P]
     lib.hrw_smem_reduce.argtypes = [VP, i32, P, P, u32, u32, i32, P]
-    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce, lib.hrw_probe, lib.hrw_trace_probe,
-              lib.hrw_smem_reduce):
+    for f in (lib.hrw_stencil, lib.hrw_histogram, lib.hrw_reduce, lib.hrw_smem_reduce):
         f.restype = i32
     _wl = lib
     return lib
@@ -476,68 +473,3 @@ def run_reduce(view, d_data, block=256, drop_level=-1, stream=None):
     if rc:
         raise RuntimeError("hrw_reduce failed (%d)" % rc)
 
-
-PROBE_MODES = ("load", "cas64", "load+cas64", "atomicAdd64", "store64")
-TRACE_PROBE_MODES = ("load", "load+cas64", "atomicAdd64", "records only")
-
-
-def probe_trace_access(trace, log2_words=(22, 23, 24, 25, 26), reps=5):
-    """Memory work of a check without ordering or state machine: every access
-    record of the device-resident `trace` touches word (word mod 2^lg) of an
-    8-byte array, per mode.  Returns {"<MB>_MB": {mode: ms}} (mean of reps)."""
-    import torch
-    lib = load_workloads()
-    ptr, n = _ptr_and_count(trace)
-    device = trace.device
-    a = torch.zeros(1 << max(log2_words), dtype=torch.int64, device=device)
-    sink = torch.zeros(1, dtype=torch.int64, device=device)
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    stream = torch.cuda.current_stream(device)
-    out = {}
-    for lg in log2_words:
-        row = {}
-        for mode, name in enumerate(TRACE_PROBE_MODES):
-            times = []
-            for r in range(reps + 1):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                rc = lib.hrw_trace_probe(mode, ptr, n, a.data_ptr(), lg, sink.data_ptr(), sms * 4, 256,
-                                         stream.cuda_stream)
-                e1.record(stream)
-                torch.cuda.synchronize(device)
-                if rc:
-                    raise RuntimeError("hrw_trace_probe failed (%d)" % rc)
-                if r:
-                    times.append(e0.elapsed_time(e1))
-            row[name] = round(sum(times) / len(times), 4)
-        out["%d_MB" % ((8 << lg) >> 20)] = row
-    return out
-
-
-def probe_random_access(device, log2_words=(21, 23, 24, 25, 26), total=1 << 26, reps=3):
-    """Random 8-byte access rates (G ops/s) over arrays of 2^lg words, per mode."""
-    import torch
-    lib = load_workloads()
-    n = 1 << max(log2_words)
-    a = torch.zeros(n, dtype=torch.int64, device=device)
-    sink = torch.zeros(1, dtype=torch.int64, device=device)
-    sms = torch.cuda.get_device_properties(device).multi_processor_count
-    stream = torch.cuda.current_stream(device)
-    out = {}
-    for lg in log2_words:
-        row = {}
-        for mode, name in enumerate(PROBE_MODES):
-            times = []
-            for r in range(reps + 1):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                rc = lib.hrw_probe(mode, a.data_ptr(), lg, total, sink.data_ptr(), sms * 8, 256, stream.cuda_stream)
-                e1.record(stream)
-                torch.cuda.synchronize(device)
-                if rc:
-                    raise RuntimeError("hrw_probe failed (%d)" % rc)
-                if r:
-                    times.append(e0.elapsed_time(e1))
-            row[name] = total / (sum(times) / len(times) / 1e3) / 1e9
-        out["%d_MB" % ((8 << lg) >> 20)] = row
-    return out

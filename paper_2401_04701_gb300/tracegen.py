@@ -154,7 +154,13 @@ def gen_tree_reduction(seed: int, inject: bool = True, segments: int = 48, block
     for k in range(1, n_epochs):
         bc_of_epoch[k] = bc_of_epoch[k - 1] + (0 if dropped[k - 1] else 1)
 
+    # Records in SIMT log order: epoch by epoch, its barrier records (thread
+    # order) first, then its accesses ordered by warp, instruction (rep, seg,
+    # j) and lane; built directly in that order, block_dim a multiple of 32
+    # (else lane-major inside one ragged warp, the same order).
     t_all = np.arange(block_dim)
+    nwarp = -(-block_dim // 32)
+    wl = np.arange(nwarp * 32).reshape(nwarp, 32)           # thread id of (warp, lane)
     parts = []
     for k in range(n_epochs):
         s = (block_dim // 2) >> k
@@ -164,30 +170,23 @@ def gen_tree_reduction(seed: int, inject: bool = True, segments: int = 48, block
             sync["tid"] = t_all
             sync["bc"] = bc
             sync["op"] = OP_SYNCTHREADS
-            parts.append((np.full(block_dim, bc), np.full(block_dim, k), np.zeros(block_dim), sync))
-        # accesses: grid over (rep, seg, j, t)
-        rep, seg, j, t = np.meshgrid(np.arange(reps), np.arange(segments), np.arange(3), t_all,
-                                     indexing="ij")
-        rep, seg, j, t = rep.ravel(), seg.ravel(), j.ravel(), t.ravel()
-        bound = np.where(doubled[seg, k], 2 * s, s)
-        keep = t < bound
-        rep, seg, j, t = rep[keep], seg[keep], j[keep], t[keep]
+            parts.append(sync)
+        # grid over (warp, rep, seg, j, lane), kept where t < the unit's active bound
+        shape = (nwarp, reps, segments, 3, 32)
+        t = np.broadcast_to(wl.reshape(nwarp, 1, 1, 1, 32), shape)
+        seg = np.broadcast_to(np.arange(segments).reshape(1, 1, -1, 1, 1), shape)
+        j = np.broadcast_to(np.arange(3).reshape(1, 1, 1, 3, 1), shape)
+        bound = np.where(doubled[:, k], 2 * s, s).reshape(1, 1, -1, 1, 1)
+        keep = (t < bound) & (t < block_dim)
+        t, seg, j = t[keep], seg[keep], j[keep]
         idx = np.where(j == 1, (t + s) % block_dim, t)
         rec = np.zeros(len(t), RECORD)
         rec["word"] = seg * block_dim + idx
         rec["tid"] = t
         rec["bc"] = bc
         rec["op"] = np.where(j == 2, OP_W, OP_R)
-        # SIMT log order inside the epoch: warp, instruction (rep, seg, j), lane
-        step = (rep * segments + seg) * 3 + j + 1
-        parts.append((np.full(len(t), bc), np.full(len(t), k), (t // 32) * (1 << 32) + step * 64 + (t % 32),
-                      rec))
-    bcs = np.concatenate([p[0] for p in parts])
-    eps = np.concatenate([p[1] for p in parts])
-    sub = np.concatenate([p[2] for p in parts]).astype(np.int64)
-    recs = np.concatenate([p[3] for p in parts])
-    order = np.lexsort((sub, eps, bcs))
-    trace = recs[order]
+        parts.append(rec)
+    trace = np.concatenate(parts) if parts else np.zeros(0, RECORD)
     info = dict(n_words=n_words, block_dim=block_dim, n_threads=block_dim,
                 doubled=[(int(a), int(b)) for a, b in zip(*np.nonzero(doubled))],
                 dropped=[int(x) for x in np.flatnonzero(dropped)])
@@ -434,6 +433,18 @@ def smem_reduce_program(n: int, block: int, drop_level: int = -1) -> np.ndarray:
 # Workload 3: power-law graph, push-style relaxation
 # --------------------------------------------------------------------------
 
+def _sample_cdf(cdf: np.ndarray, u: np.ndarray, n: int) -> np.ndarray:
+    """Inverse-CDF sampling: the index i with cdf[i-1] <= u < cdf[i], capped at
+    n - 1; the lookups run in chunks on host threads (same result as one call)."""
+    from concurrent.futures import ThreadPoolExecutor
+    chunks = np.array_split(u, max(1, min(64, len(u) >> 16)))
+    with ThreadPoolExecutor(min(16, len(chunks))) as ex:
+        parts = list(ex.map(lambda c: np.searchsorted(cdf, c, side="right"), chunks))
+    out = np.concatenate(parts).astype(np.int64) if parts else np.zeros(0, np.int64)
+    np.minimum(out, n - 1, out=out)
+    return out
+
+
 def gen_powerlaw_push(seed: int, log2_vertices: int = 22, avg_degree: int = 16, sweeps: int = 4,
                       gamma: float = 2.1, block_dim: int = 256, inject_frac: float = 0.0005,
                       inject: bool = True):
@@ -458,25 +469,30 @@ def gen_powerlaw_push(seed: int, log2_vertices: int = 22, avg_degree: int = 16, 
     w = (np.arange(1, n + 1, dtype=np.float64)) ** (-1.0 / (gamma - 1.0))
     cdf = np.cumsum(w)
     cdf /= cdf[-1]
-    src = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
-    dst = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
-    np.minimum(src, n - 1, out=src)
-    np.minimum(dst, n - 1, out=dst)
-    order = np.argsort(src, kind="stable")
+    src = _sample_cdf(cdf, rng.random(m), n)
+    dst = _sample_cdf(cdf, rng.random(m), n)
+    # CSR order: edges stably sorted by source (the key src * 2^k + edge index
+    # is unique, so an unstable sort of it is the stable order by source)
+    kbits = max(1, int(m - 1).bit_length())
+    key = (src.astype(np.uint64) << np.uint64(kbits)) | np.arange(m, dtype=np.uint64)
+    key.sort()
+    order = (key & np.uint64((1 << kbits) - 1)).astype(np.int64)
+    del key
     src = src[order].astype(np.uint32)
     dst = dst[order].astype(np.uint32)
     del order
     per = 2 * m
     trace = np.zeros(per * sweeps, RECORD)
-    for k in range(sweeps):
-        part = trace[k * per:(k + 1) * per]
-        part["tid"][0::2] = src
-        part["tid"][1::2] = src
-        part["word"][0::2] = src
-        part["word"][1::2] = dst
-        part["op"] = OP_A
-        part["flags"][0::2] = FLAG_ATOMIC_LOAD
-        part["kernel"] = k
+    first = trace[:per]
+    first["tid"][0::2] = src
+    first["tid"][1::2] = src
+    first["word"][0::2] = src
+    first["word"][1::2] = dst
+    first["op"] = OP_A
+    first["flags"][0::2] = FLAG_ATOMIC_LOAD
+    for k in range(1, sweeps):
+        trace[k * per:(k + 1) * per] = first
+        trace["kernel"][k * per:(k + 1) * per] = k
     injected = np.zeros(0, np.int64)
     if inject:
         n_inj = int(inject_frac * m * sweeps)

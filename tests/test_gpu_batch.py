@@ -135,6 +135,36 @@ def test_uneven_batch_workload(oracle_mod, hr):
             assert status == hr.HR_OK and hr.race_keys(races) == want, i
 
 
+@pytest.mark.slow
+def test_full_batch_workload_equals_oracle(oracle_mod, hr):
+    """The batch workload at full size: 512 traces (lengths log-uniform 10K..10M,
+    600.6M records, 60% shared-memory and 40% global-memory traces) in one
+    batched launch, the way bench.py times it; every trace's race set equals the
+    oracle's brute force on that trace, and one launch per trace gives the same."""
+    from concurrent.futures import ThreadPoolExecutor
+    jobs = tg.gen_batch(tg.seed_for(4))
+    assert len(jobs) == 512
+    with ThreadPoolExecutor(len(__import__("os").sched_getaffinity(0))) as ex:
+        want = list(ex.map(lambda j: oracle_mod.race_keys(oracle_mod.bruteforce(j[0], j[1]["block_dim"])), jobs))
+    regions = [dict(n_words=info["n_words"], block_dim=info["block_dim"]) for _, info in jobs]
+    dev = [to_dev(tr) for tr, _ in jobs]
+    del jobs
+    with hr.Checker(regions, report_capacity=1 << 18) as ck:
+        ck.batch_reserve(len(dev), 1 << 18)
+        ck.check_batch(list(enumerate(dev)))
+        for i in range(len(dev)):
+            races, status, n_total, _ = ck.report(i)
+            assert status == hr.HR_OK and n_total == len(want[i]) and hr.race_keys(races) == want[i], i
+        for i in range(len(dev)):
+            ck.reset(i)
+        for i, d in enumerate(dev):
+            ck.check_trace(i, d)
+        for i in range(len(dev)):
+            races, status, n_total, _ = ck.report(i)
+            assert status == hr.HR_OK and hr.race_keys(races) == want[i], i
+    assert sum(len(x) for x in want) > 0
+
+
 def test_batch_job_completion_times(hr):
     """hr_batch_job_times: one device-clock completion time per job of the last
     batch; an empty trace reads 0; no job ends after the batch's own span, and

@@ -230,12 +230,43 @@ def test_powerlaw_push_small(oracle_mod, hr, aggregate):
         assert cnt["merged"] > 0          # repeated dist[src] reads fold into one update
 
 
-@pytest.mark.slow
-def test_powerlaw_push_full_size_sampled(oracle_mod, hr):
-    """2^22 vertices, 2^26 edges, 4 sweeps (536,870,912 records): GPU races on a
-    sample of words (every injected word plus random ones) equal the oracle run
-    on just those words' records."""
+@pytest.fixture(scope="module")
+def powerlaw_full(oracle_mod):
+    """The power-law push workload at full size (2^22 vertices, 2^26 edges, 4
+    sweeps: 536,870,912 records) and the oracle's complete race set, computed
+    by the brute force on disjoint word ranges over all host cores."""
     tr, info = tg.gen_powerlaw_push(tg.seed_for(3))
+    bf = oracle_mod.bruteforce_parallel(tr, info["block_dim"], info["n_words"])
+    return tr, info, oracle_mod.race_keys(bf)
+
+
+@pytest.mark.slow
+def test_powerlaw_push_full_size(oracle_mod, hr, powerlaw_full):
+    """Every racy (kernel, word, epoch) of the full trace, hub words included,
+    for the autotuned variant (as bench.py runs it), the plain kernel and the
+    warp-aggregated kernel."""
+    tr, info, want = powerlaw_full
+    assert len(want) > 0
+    d = to_dev(tr)
+    with hr.Checker([dict(n_words=info["n_words"], block_dim=info["block_dim"])], report_capacity=1 << 24) as ck:
+        ck.autotune(0, d)
+        for agg in (None, True, False):
+            ck.reset(0)
+            if agg is None:
+                ck.check_trace(0, d)
+            else:
+                ck.check_trace(0, d, aggregate=agg)
+            races, status, n_total, _ = ck.report(0)
+            assert status == hr.HR_OK and n_total == len(races) == len(want), agg
+            assert hr.race_keys(races) == want, agg
+
+
+@pytest.mark.slow
+def test_powerlaw_push_full_size_sampled(oracle_mod, hr, powerlaw_full):
+    """The same trace, checked against the oracle run on a sample of words
+    (every injected word's records plus random words) on their own: a word's
+    result depends on its records alone."""
+    tr, info, want_all = powerlaw_full
     races, status, n_total, _, _ = gpu_check(hr, tr, info["n_words"], info["block_dim"], cap=1 << 24)
     assert status == hr.HR_OK and n_total == len(races)
     rng = np.random.default_rng(9)
@@ -245,9 +276,9 @@ def test_powerlaw_push_full_size_sampled(oracle_mod, hr):
     keep = np.isin(tr["word"], sample)
     sub = tr[keep]
     want = oracle_mod.race_keys(oracle_mod.bruteforce(sub, info["block_dim"]))
-    got = {k for k in hr.race_keys(races) if k[1] in set(sample.tolist())}
-    assert got == want
-    # every kernel's racy words include the injected words whose write meets another thread
+    words = set(sample.tolist())
+    got = {k for k in hr.race_keys(races) if k[1] in words}
+    assert got == want == {k for k in want_all if k[1] in words}
     assert len(want) > 0
 
 
