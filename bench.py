@@ -419,21 +419,22 @@ def batch_workload(dev, reps=3):
     return out
 
 
-def serving_workload(dev, duration, rates=(2000.0, 8000.0)):
-    """The serving measurement at the workload's 2000 requests/s and at a higher
-    rate where one-at-a-time service saturates."""
+def serving_workload(dev, duration, rates=(2000.0,), serial_duration=None):
+    """The serving measurement at the workload's 2000 requests/s (and, with
+    --all-workloads, at a higher rate where one-at-a-time service saturates)."""
     from paper_2401_04701_gb300 import serving
     pool = serving.TracePool(dev, scale="full")
-    return {"%d_per_s" % r: serving_run(dev, pool, duration, r) for r in rates}
+    return {"%d_per_s" % r: serving_run(dev, pool, duration, r, serial_duration) for r in rates}
 
 
-def serving_run(dev, pool, duration, rate):
+def serving_run(dev, pool, duration, rate, serial_duration=None):
     """Poisson arrivals (rate/s for `duration` s): 75% trace checks (prefixes of
     10K..50M records of pooled tree-reduction, global-mix and power-law traces),
-    25% instrumented kernels (grid 64..4096 x 256); 64 region slots, 64 GB
-    shadow budget, 64M records per iteration shared by the active jobs (at
-    least 1M each).  Then the same arrivals served one request at a time (whole
-    trace per check) for at most twice as long."""
+    25% instrumented kernels (grid 64..4096 x 256, on streams of their own); 64
+    region slots, 64 GB shadow budget, 64M records per iteration shared by the
+    active jobs (at least 1M each).  Then the same arrivals (the first
+    `serial_duration` seconds of them, default all) served one request at a
+    time (whole trace per check) for at most twice as long."""
     from paper_2401_04701_gb300 import serving
     reqs = serving.make_requests(tg_seed(5), rate=rate, duration=duration)
     srv = serving.Server(pool, dev, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30, chunk_records=1 << 20)
@@ -441,13 +442,16 @@ def serving_run(dev, pool, duration, rate):
     res = srv.run(reqs)
     wall = time.perf_counter() - t0
     out = {"requests": len(reqs), "rate_per_s": rate, "duration_s": duration,
-           "continuous_batching": dict(serving.summarize(res, wall), iterations=srv.iterations, wall_s=wall)}
+           "continuous_batching": dict(serving.summarize(res, wall), iterations=srv.iterations, wall_s=wall,
+                                       overlapped_launches=srv.overlapped)}
+    sd = duration if serial_duration is None else min(duration, serial_duration)
+    sreqs = [r for r in reqs if r.arrival <= sd]
     ser = serving.Server(pool, dev, n_slots=2, slot_words=1 << 26, budget_bytes=64 << 30)
     t0 = time.perf_counter()
-    sres = ser.run_serial(reqs, time_limit=2 * duration)
+    sres = ser.run_serial(sreqs, time_limit=2 * sd)
     swall = time.perf_counter() - t0
-    out["serial_one_at_a_time"] = dict(serving.summarize(sres, swall), wall_s=swall,
-                                       not_served=len(reqs) - len(sres))
+    out["serial_one_at_a_time"] = dict(serving.summarize(sres, swall), wall_s=swall, requests=len(sreqs),
+                                       arrivals_s=sd, not_served=len(sreqs) - len(sres))
     return out
 
 
@@ -667,10 +671,17 @@ def run_gpu(args, rank, world, local_rank):
         line["every_epoch_reports"] = every_epoch_workload(dev, d_trace, info, n_acc, n_sync, p_hbm)
     if not args.no_instrumented:
         line["instrumented_slowdown"] = instrumented_slowdown(dev)
-    if args.all_workloads:
+    if not args.quick:
+        # the other workloads: tree reduction and power-law push (per-wave and
+        # autotuned, plain vs warp-aggregated), the 512-trace batch (one launch
+        # per trace vs one batched launch vs CUDA-graph replay), and serving at
+        # 2000 requests/s (continuous batching vs one request at a time)
+        t0 = time.perf_counter()
         line["other_workloads"] = other_workloads(dev)
         line["batch_workload"] = batch_workload(dev)
-        line["serving"] = serving_workload(dev, args.serving_seconds)
+        rates = (2000.0, 8000.0) if args.all_workloads else (2000.0,)
+        line["serving"] = serving_workload(dev, args.serving_seconds, rates, args.serial_seconds)
+        line["other_workloads_wall_s"] = time.perf_counter() - t0
     print(json.dumps(line), flush=True)
     ck.close()
 
@@ -684,11 +695,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-instrumented", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the global-mix line (no tree, power-law, batch or serving runs)")
     ap.add_argument("--all-workloads", action="store_true",
-                    help="also time the tree-reduction and power-law workloads (adds ~2 min)")
+                    help="also serve 8000 requests/s (over capacity for one-at-a-time service)")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving measurement")
-    ap.add_argument("--serving-seconds", type=float, default=10.0,
-                    help="length of the Poisson arrival run in --all-workloads (60 for the full run)")
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
+                    help="length of the Poisson arrival run (the serving workload is 60 s)")
+    ap.add_argument("--serial-seconds", type=float, default=60.0,
+                    help="arrivals the one-request-at-a-time baseline serves (the first this many seconds)")
     ap.add_argument("--latency-checks", type=int, default=50,
                     help="single checks timed one at a time for the p50/p99 check latency (default workload)")
     ap.add_argument("--variant", type=int, default=None,

@@ -302,6 +302,20 @@ typedef struct hr_filter {
     uint32_t lane_mask; /* monitored lanes of each warp (bit l: lane l = tid mod block_dim mod
                            warp_size); 0xFFFFFFFF = every lane, 0 is invalid */
     uint32_t reserved;  /* must be 0 */
+    /* Symmetric work group (Sec. IV-A: only representative threads of a
+     * user-declared symmetric group are tracked).  Blocks [sym_lo, sym_hi)
+     * are declared to run the same program, block sym_lo + m on the words of
+     * block sym_lo shifted up by m * sym_stride.  An access of thread tid of
+     * block sym_lo + m to word w is applied as the access of thread
+     * tid - m * block_dim (the same thread of block sym_lo) to word
+     * w - m * sym_stride (not monitored if w < m * sym_stride); the block
+     * range, lane mask and word window then apply to that representative
+     * access, and a race on it is reported with the representative's tid and
+     * word.  With a word window over the representative's data the shadow
+     * shrinks by the group size.  sym_hi 0 = no group. */
+    uint32_t sym_lo;
+    uint32_t sym_hi;
+    uint64_t sym_stride;
 } hr_filter;
 
 /*
@@ -310,7 +324,12 @@ typedef struct hr_filter {
  * records keep absolute word indices.  Stream-ordered; the filter stays set
  * across hr_reset and is cleared by hr_region_reconfigure.  HR_ERR_INVALID if
  * the window is empty or wider than the region, block_hi < block_lo (with
- * block_hi != 0), lane_mask is 0 or reserved is not 0.
+ * block_hi != 0), sym_hi <= sym_lo (with sym_hi != 0), lane_mask is 0 or
+ * reserved is not 0.  A symmetric group finds the races inside each member
+ * block, exactly when the members are symmetric; it misses races between two
+ * members and races of other blocks on a member's (non-representative)
+ * words, and if the members are not symmetric it may report races that only
+ * the folded program has.
  */
 hr_status hr_set_filter(hr_ctx* ctx, uint32_t region, const hr_filter* filter, hr_stream_t stream);
 

@@ -236,17 +236,31 @@ static __device__ __forceinline__ uint32_t hr_ld_relaxed32(const unsigned int* p
 static __device__ __forceinline__ uint32_t hr_wc_bits(const hr_geom& g) { return (24u - g.tid_bits) >> 1; }
 static __device__ __forceinline__ uint32_t hr_bc_bits(const hr_geom& g) { return 24u - g.tid_bits - hr_wc_bits(g); }
 
-/* Whether a filter selects only part of the accesses. */
+/* Whether a filter selects only part of the accesses (or folds a symmetric group). */
 static __device__ __forceinline__ bool hr_filter_active(const hr_filter& f)
 {
-    return f.word_hi != 0 || f.block_hi != 0 || f.lane_mask != 0xFFFFFFFFu;
+    return f.word_hi != 0 || f.block_hi != 0 || f.lane_mask != 0xFFFFFFFFu || f.sym_hi != 0;
 }
 
-/* Whether thread tid's access to `word` is monitored under filter f; *idx gets
- * the shadow index of the word (word - word_lo inside a window). */
-static __device__ __forceinline__ bool hr_monitored(const hr_filter& f, const hr_geom& g, uint32_t tid,
+/* Whether thread *tid's access to `word` is monitored under filter f; *idx gets
+ * the shadow index of the word (word - word_lo inside a window).  A member of
+ * the filter's symmetric group is first folded onto the group's
+ * representative block: *tid and the word become the representative's. */
+static __device__ __forceinline__ bool hr_monitored(const hr_filter& f, const hr_geom& g, uint32_t* tid_io,
                                                     unsigned long long word, unsigned long long* idx)
 {
+    uint32_t tid = *tid_io;
+    if (f.sym_hi != 0) {
+        const uint32_t b = g.bd_shift != ~0u ? tid >> g.bd_shift : hr_fastdiv(tid, g.bd_magic);
+        if (b > f.sym_lo && b < f.sym_hi) {
+            const uint32_t m = b - f.sym_lo;
+            const unsigned long long shift = (unsigned long long)m * f.sym_stride;
+            if (word < shift) return false;
+            word -= shift;
+            tid -= m * g.block_dim;
+            *tid_io = tid;
+        }
+    }
     *idx = word;
     if (f.word_hi != 0) {
         if (word < f.word_lo || word >= f.word_hi) return false;
@@ -507,18 +521,20 @@ static __device__ __forceinline__ void hr_syncwarp(hr_clock& c)
 static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long long word, uint32_t op,
                                                  const hr_clock& c)
 {
-    const unsigned long long abs_word = word;
-    if (hr_filter_active(v.filter) && !hr_monitored(v.filter, v.geom, c.tid, abs_word, &word)) return;
+    hr_clock cf = c;  // the representative's thread when a symmetric group folds this one
+    if (hr_filter_active(v.filter) && !hr_monitored(v.filter, v.geom, &cf.tid, word, &word)) return;
+    // the word races are reported on (absolute, the representative's under a symmetric group)
+    const unsigned long long abs_word = word + (v.filter.word_hi != 0 ? v.filter.word_lo : 0ull);
     if (word >= v.n_words || op > HR_A) {
         hr_set_error(v.error, word >= v.n_words ? HR_ERR_RANGE : HR_ERR_UNSUPPORTED);
         return;
     }
-    if (!hr_fits(c.tid, c.bc, c.wc, v.geom)) {
+    if (!hr_fits(cf.tid, cf.bc, cf.wc, v.geom)) {
         hr_set_error(v.error, HR_ERR_CLOCK_OVERFLOW);
         return;
     }
     if (v.geom.report_mode == HR_REPORT_EVERY_EPOCH) {
-        const uint32_t st = hr_ep_apply(v.shadow, v.n_words, word, (uint32_t)abs_word, c.tid, op, c.bc, c.wc,
+        const uint32_t st = hr_ep_apply(v.shadow, v.n_words, word, (uint32_t)abs_word, cf.tid, op, cf.bc, cf.wc,
                                         v.kernel, v.geom, v.ring, v.ring_cap, v.n_races, v.flags, v.region,
                                         HR_CAS_RETRY_CAP);
         if (st) hr_set_error(v.error, st);
@@ -528,12 +544,12 @@ static __device__ __forceinline__ void hr_access(const hr_view& v, unsigned long
     uint64_t o = hr_shadow_load(v.shadow, word, v.geom);
     for (int it = 0; it < HR_CAS_RETRY_CAP; ++it) {
         uint32_t raced = 0;
-        const uint64_t n = hr_fsm_step(o, c.tid, op, c.bc, c.wc, ktag, v.geom, v.table, &raced);
+        const uint64_t n = hr_fsm_step(o, cf.tid, op, cf.bc, cf.wc, ktag, v.geom, v.table, &raced);
         if (n == o) return;
         const uint64_t prev = hr_shadow_cas(v.shadow, word, o, n, v.geom);
         if (prev == o) {
             if (raced)
-                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)abs_word, c.tid, v.kernel, c.bc,
+                hr_append_race(v.ring, v.ring_cap, v.n_races, v.flags, (uint32_t)abs_word, cf.tid, v.kernel, cf.bc,
                                v.region, op, raced - 1u);
             return;
         }

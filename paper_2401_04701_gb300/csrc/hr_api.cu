@@ -10,6 +10,9 @@
 
 namespace {
 
+// the Python binding mirrors these layouts (paper_2401_04701_gb300/hirace.py)
+static_assert(sizeof(hr_filter) == 48 && sizeof(hr_view) == 168, "hr_filter / hr_view layouts");
+
 struct RegionHost {
     hr_region_desc desc{};
     hr_region_dev* d = nullptr;           // element of the context's device region array
@@ -25,6 +28,7 @@ struct RegionHost {
     bool owns_ring = true;
     cudaEvent_t done = nullptr;           // recorded after every call on the region
     bool captured = false;                // work was queued inside a stream capture
+    bool views = false;                   // a device view was handed out (inline writes possible)
     void* bin_mem = nullptr;              // binned checker tables (allocated by its first check)
     hr_bin bin{};                         // carved out of bin_mem; bin.out is its own allocation
 };
@@ -309,7 +313,7 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     job.kb = (unsigned long long)kernel_base << 32;
     job.region = region;
     job.int_begin = 0;
-    hr_plan_intervals(n, HR_MAX_INTERVALS, &job.G, &job.n_int);
+    hr_plan_intervals(n, HR_SMALL_INTERVALS, &job.G, &job.n_int);
     ProfiledCall pc{};
     if (ctx->profile) pc = take_events(ctx);
     if (ctx->profile) cudaEventRecord(pc.begin, s);
@@ -317,6 +321,7 @@ static hr_status check_common(hr_ctx* ctx, uint32_t region, const hr_record* d_t
     w.wait_ns = ctx->wait_ns;
     w.cas_cap = ctx->cas_cap;
     w.test_flags = ctx->test_flags;
+    w.views = r.views ? 1u : 0u;
     unsigned variant = ctx->variant;
     if (!aggregate && variant < HR_N_SHAPES) variant |= 1u;  // odd ids do not aggregate (nor does the binned one)
     if (r.desc.report_mode == HR_REPORT_EVERY_EPOCH) variant = HR_EVERY_EPOCH_VARIANT;
@@ -608,6 +613,7 @@ extern "C" hr_status hr_set_filter(hr_ctx* ctx, uint32_t region, const hr_filter
         return HR_ERR_INVALID;
     if (f.word_hi > (1ull << 32)) return HR_ERR_INVALID;  // record word indices are 32-bit
     if (f.block_hi != 0 && f.block_hi < f.block_lo) return HR_ERR_INVALID;
+    if (f.sym_hi != 0 && f.sym_hi <= f.sym_lo) return HR_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     (void)cudaGetLastError();  // report only errors of this call's launches
     cudaError_t e = hr_launch_set_filter(r.d, f, s);
@@ -631,6 +637,7 @@ extern "C" hr_status hr_device_view(hr_ctx* ctx, uint32_t region, hr_view* out)
     if (!valid_region(ctx, region) || !out) return HR_ERR_INVALID;
     RegionHost& r = ctx->regions[region];
     hr_region_dev* d = r.d;
+    r.views = true;
     out->shadow = r.shadow;
     out->ring = r.ring;
     out->n_races = &d->n_races;

@@ -43,6 +43,11 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <cstddef>
+#include <cstdlib>
+#include <cstring>
+#include <type_traits>
+
 #include "hr_internal.h"
 
 namespace cg = cooperative_groups;
@@ -53,6 +58,9 @@ constexpr unsigned STREAM_THREADS = 1024;      // threads of the two streaming p
 constexpr unsigned STREAM_R = 4;               // records each streaming thread loads per step
 constexpr unsigned STREAM_STEP = STREAM_THREADS * STREAM_R;
 constexpr unsigned SCAN_THREADS = 1024;
+// 4-byte bucketed access: tid << (SEG_SHIFT + 2) | op << SEG_SHIFT | word within the segment
+constexpr unsigned PACK4_TID_SHIFT = HR_BIN_SEG_SHIFT + 2;
+constexpr unsigned PACK4_TID_LIMIT = 1u << (32 - PACK4_TID_SHIFT);
 
 // whether this check is one the binned checker takes (read from the pre-pass
 // results; every kernel below decides the same way)
@@ -118,11 +126,12 @@ __device__ __forceinline__ BinAcc bin_decode(const uint4 v, bool in, unsigned lo
     const unsigned flags = v.w >> 24;
     const bool same_wave = v.z == bcwc && (v.w & 0xFFFFu) + kb == kern;
     bool a = in && op <= HR_A;
-    unsigned widx = v.x;
+    // (a symmetric group folds the access onto its representative: tid, widx)
+    unsigned widx = v.x, tid = v.y;
     bool mon = true;
     if (filtering && a && same_wave) {
         unsigned long long ix = v.x;
-        mon = hr_monitored(f, g, v.y, v.x, &ix);
+        mon = hr_monitored(f, g, &tid, v.x, &ix);
         widx = (unsigned)ix;
     }
     if (in) {
@@ -133,13 +142,13 @@ __device__ __forceinline__ BinAcc bin_decode(const uint4 v, bool in, unsigned lo
             r.err = HR_ERR_RANGE;
     }
     a = a && same_wave && mon && widx < n_words;
-    if (a && !(clocks_fit && (g.shadow_bytes != 4 || (v.y >> g.tid_bits) == 0))) {
+    if (a && !(clocks_fit && (g.shadow_bytes != 4 || (tid >> g.tid_bits) == 0))) {
         r.err = HR_ERR_CLOCK_OVERFLOW;
         a = false;
     }
     r.act = a;
     r.seg = widx >> HR_BIN_SEG_SHIFT;
-    r.rec = make_uint2(v.y, (op << 16) | (widx & (HR_BIN_SEG - 1u)));
+    r.rec = make_uint2(tid, (op << 16) | (widx & (HR_BIN_SEG - 1u)));
     return r;
 }
 
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(STREAM_THREADS) hr_bin_count(hr_region_dev* __
     stream_prologue(w, jb, W, S);
     const unsigned P = S.n_parts, tx = threadIdx.x, lane = tx & 31;
     if (blockIdx.x == 0 && tx == 0) w.ctl->bin_parts = P;
-    unsigned err = 0;
+    unsigned err = 0, max_tid = 0;
     for (unsigned k = 0; k < S.np; ++k) {
         const unsigned gw = S.w0 + k, part = S.p0 + k;
         const unsigned long long pa = max(S.a, S.start[gw]), pb = min(S.b, S.start[gw + 1]);
@@ -293,7 +302,10 @@ __global__ void __launch_bounds__(STREAM_THREADS) hr_bin_count(hr_region_dev* __
                 const uint4 v = in ? S.tile[buf][j * STREAM_THREADS + tx] : make_uint4(0u, 0u, 0u, 0u);
                 const BinAcc r = bin_decode(v, in, key, kb, g, f, filtering, n_words, fit);
                 if (r.err) err = r.err;
-                if (r.act) atomicAdd(&S.seg[r.seg], 1u);
+                if (r.act) {
+                    atomicAdd(&S.seg[r.seg], 1u);
+                    max_tid = max(max_tid, r.rec.x);
+                }
             }
         }
         __syncthreads();
@@ -302,6 +314,9 @@ __global__ void __launch_bounds__(STREAM_THREADS) hr_bin_count(hr_region_dev* __
         __syncthreads();
     }
     if (err) hr_set_error(&rg->error, err);
+    // the largest thread id decides the packing of the bucketed accesses
+    for (int o = 16; o > 0; o >>= 1) max_tid = max(max_tid, __shfl_xor_sync(0xFFFFFFFFu, max_tid, o));
+    if (lane == 0 && max_tid) atomicMax(&w.ctl->bin_max_tid, max_tid);
 }
 
 // ------------------------------------------------------------ 2-3. scan
@@ -318,7 +333,30 @@ __global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan_sums(hr_work w)
             if (st.type == HR_STAGE_RECORDS)
                 w.bin.clear[st.wave - wb] = s > 0 && w.stages[s - 1].type == HR_STAGE_CLEAR;
         }
-        if (threadIdx.x == 0) w.ctl->binned = 1;
+        // the largest bc and wc of the check's waves, for the working-shadow packing
+        __shared__ unsigned s_max_bc, s_max_wc;
+        if (threadIdx.x == 0) s_max_bc = s_max_wc = 0;
+        __syncthreads();
+        const unsigned W = w.ctl->n_waves, wb0 = w.jobs[0].wave_begin;
+        for (unsigned i = threadIdx.x; i < W; i += blockDim.x) {
+            const unsigned k = (unsigned)w.wave_key[wb0 + i];
+            atomicMax(&s_max_bc, k >> 16);
+            atomicMax(&s_max_wc, k & 0xFFFFu);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            w.ctl->binned = 1;
+            const unsigned mt = w.ctl->bin_max_tid;
+            w.ctl->bin_pack4 = mt < PACK4_TID_LIMIT;
+            w.ctl->seg_ticket = 0;
+            // a 4-byte working shadow (tid in tb bits, wc and bc in the rest of 24) when
+            // nothing in the region is live and the check's tids and clocks fit it
+            unsigned tb = 1;
+            while (tb < 24 && (mt >> tb)) ++tb;
+            const unsigned wcb = (24 - tb) / 2, bcb = 24 - tb - wcb;
+            const bool fits = tb <= 22 && s_max_wc < (1u << wcb) && s_max_bc < (1u << bcb);
+            w.ctl->bin_tbits = (w.ctl->fresh && fits) ? tb : 0u;
+        }
     }
     const unsigned long long E = (unsigned long long)w.bin.n_seg * w.ctl->bin_parts;
     const unsigned long long b0 = (unsigned long long)blockIdx.x * HR_BIN_SCAN;
@@ -440,6 +478,8 @@ __global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_
             w_hi = max(w_hi, S.w0[r] + S.np[r]);
         }
     const unsigned my_segs = (n_seg + CL - 1 - rank) / CL;  // segments s with s % CL == rank
+    const bool pack4 = w.ctl->bin_pack4 != 0;
+    unsigned* out4 = reinterpret_cast<unsigned*>(w.bin.out);
     for (unsigned gw = w_lo; gw < w_hi; ++gw) {
         // the cluster's first part of this wave: the first of its CTAs that met it
         unsigned fp = 0;
@@ -472,14 +512,19 @@ __global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_
                     unsigned* c = cluster.map_shared_rank(&S.cur[r.seg / CL], r.seg % CL);
                     pos[j] = atomicAdd(c, (unsigned)__popc(m));
                 }
-                rec[j] = make_uint2(r.rec.x, r.rec.y | (gw << 24));  // the wave rides along (W <= 256)
+                rec[j] = r.rec;
                 grp[j] = m;
                 act[j] = r.act;
             }
 #pragma unroll
             for (unsigned j = 0; j < SCATTER_R; ++j) {
                 const unsigned p = __shfl_sync(0xFFFFFFFFu, pos[j], __ffs(grp[j]) - 1);
-                if (act[j]) w.bin.out[p + __popc(grp[j] & ((1u << lane) - 1u))] = rec[j];
+                const unsigned slot = p + __popc(grp[j] & ((1u << lane) - 1u));
+                if (act[j]) {
+                    if (pack4) out4[slot] = (rec[j].x << PACK4_TID_SHIFT) | ((rec[j].y >> 16) << HR_BIN_SEG_SHIFT) |
+                                            (rec[j].y & (HR_BIN_SEG - 1u));
+                    else w.bin.out[slot] = rec[j];
+                }
             }
         }
         cluster.sync();  // every add is done before the cursors are reloaded (or the CTAs exit)
@@ -522,84 +567,39 @@ static_assert((SEG_SMEM + 1024) * HR_BIN_SEG_MIN_CTAS <= 228 * 1024, "the segmen
 static_assert(HR_BIN_CHUNK * sizeof(uint2) >= HR_BIN_SEG * 4, "the compact shadow is staged in the access area");
 
 
-// POW2: the region's block size and warp size are powers of two (hr_bin::pow2),
-// and the FSM step takes its bit-operation form
-template <bool POW2>
-__global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
-    hr_bin_segments(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SegSmem& S = *reinterpret_cast<SegSmem*>(smem_raw);
-    if (!w.ctl->binned) return;
-    const hr_jobd jb = w.jobs[0];
-    hr_region_dev* rg = regions + jb.region;
-    if (*(volatile unsigned*)&rg->error) return;
-    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
-    const unsigned seg = blockIdx.x, tx = threadIdx.x;
-    // this segment's accesses: [row[0], the next row's first entry); a wave's
-    // accesses end where the next wave's first part begins
-    const unsigned* row = w.bin.table + (size_t)seg * P;
-    const unsigned r_end = seg + 1 < w.bin.n_seg ? row[P] : w.ctl->bin_total;
-    for (unsigned p = tx; p < P; p += SEG_THREADS) {
-        const unsigned wv = w.bin.part_wave[p];
-        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.wave[wv].x = p + 1 == P ? r_end : row[p + 1];
-    }
-    for (unsigned i = tx; i < W; i += SEG_THREADS) {
-        const unsigned long long key = w.wave_key[jb.wave_begin + i];
-        const unsigned kern = (unsigned)(key >> 32);
-        S.wave[i].y = ((unsigned)key & 0xFFFF0000u) | (w.bin.clear[i] ? 0x8000u : 0u) | ((kern & 7u) << 8) |
-                      ((unsigned)key & 0xFFu);
-        S.kern[i] = kern;
-    }
-    for (unsigned i = tx; i < 2048 / 4; i += SEG_THREADS)
-        reinterpret_cast<unsigned*>(S.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
-    if (tx == 0) {
-        S.r0 = row[0];
-        S.n_races = 0;
-    }
-    const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
-    const unsigned r0 = S.r0;
-    const unsigned r1 = S.wave[W - 1].x;
-    if (r0 == r1 && !any_clear) return;  // no access and no clear: the segment is untouched
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
 
-    const hr_geom g = rg->geom;
-    const unsigned long long w0 = (unsigned long long)seg * HR_BIN_SEG;
-    const unsigned nws = (unsigned)min((unsigned long long)HR_BIN_SEG, rg->n_words - w0);
-    unsigned long long* shadow = rg->shadow;
-    const bool compact = g.shadow_bytes == 4;
-    if (r0 == r1) {
-        // only clears: the segment ends cleared
-        for (unsigned i = tx; i < nws; i += SEG_THREADS) {
-            if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = 0u;
-            else shadow[w0 + i] = 0ull;
-        }
-        return;
-    }
-    // the segment's shadow (segment starts are 16-byte aligned; a ragged tail by plain loads)
-    unsigned c0 = r0, c1 = r0;  // staged accesses [c0, c1)
-    if (!compact) {
-        for (unsigned i = tx; i < nws / 2; i += SEG_THREADS) cp_async16(&S.sh[2 * i], shadow + w0 + 2 * i);
-        if ((nws & 1u) && tx == 0) S.sh[nws - 1] = shadow[w0 + nws - 1];
-        c1 = min(r0 + HR_BIN_CHUNK, r1);  // the first accesses come in with it
-        for (unsigned i = c0 + tx; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
-        cp_async_wait_all();
-        __syncthreads();
+// Stage the bucketed accesses [c0, c1) in shared memory (4 or 8 bytes each).
+template <bool PACK4>
+__device__ __forceinline__ void stage_accesses(SegSmem& S, const hr_work& w, unsigned c0, unsigned c1)
+{
+    if (PACK4) {
+        unsigned* dst = reinterpret_cast<unsigned*>(S.rec);
+        const unsigned* src = reinterpret_cast<const unsigned*>(w.bin.out);
+        for (unsigned i = c0 + threadIdx.x; i < c1; i += SEG_THREADS) cp_async4(&dst[i - c0], &src[i]);
     } else {
-        unsigned* raw = reinterpret_cast<unsigned*>(S.rec);
-        const unsigned* src = reinterpret_cast<const unsigned*>(shadow) + w0;
-        for (unsigned i = tx; i < nws / 4; i += SEG_THREADS) cp_async16(&raw[4 * i], src + 4 * i);
-        if (tx < (nws & 3u)) raw[(nws & ~3u) + tx] = src[(nws & ~3u) + tx];
-        cp_async_wait_all();
-        __syncthreads();
-        for (unsigned i = tx; i < nws; i += SEG_THREADS) S.sh[i] = hr_expand32(raw[i], g);
-        __syncthreads();
+        for (unsigned i = c0 + threadIdx.x; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
     }
+}
 
+// The segment's accesses after its shadow is in shared memory: waves in order,
+// a shared-memory CAS per access, a block barrier between waves.  PACK4: the
+// staged accesses are in the 4-byte form.  Returns the diagnostics counts.
+template <bool POW2, bool PACK4>
+__device__ __forceinline__ void apply_waves(SegSmem& S, const hr_work& w, hr_region_dev* rg, const hr_geom& g,
+                                            unsigned W, unsigned r0, unsigned r1, unsigned c0, unsigned c1,
+                                            unsigned long long word_off, unsigned* n_cas_out, unsigned* n_retry_out,
+                                            unsigned* err_out)
+{
+    constexpr unsigned CH = PACK4 ? 2 * HR_BIN_CHUNK : HR_BIN_CHUNK;  // accesses the staging area holds
+    const unsigned tx = threadIdx.x;
     const unsigned cap = w.cas_cap;
     const unsigned ring_region = rg->region;
-    const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
+    const unsigned* rec4 = reinterpret_cast<const unsigned*>(S.rec);
     unsigned n_cas = 0, n_retry = 0, err = 0;
-    const unsigned n_acc = tx == 0 ? r1 - r0 : 0u;  // every access of [r0, r1) is applied once
     unsigned b0 = r0;  // the wave's bucket starts where the previous one ended
     for (unsigned gw = 0; gw < W; ++gw) {
         const uint2 wv = S.wave[gw];
@@ -612,15 +612,25 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
         while (b0 < b1) {
             if (b0 >= c1) {  // stage the next accesses (every thread is done with the previous ones)
                 c0 = b0;
-                c1 = min(c0 + HR_BIN_CHUNK, r1);
-                for (unsigned i = c0 + tx; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
+                c1 = min(c0 + CH, r1);
+                stage_accesses<PACK4>(S, w, c0, c1);
                 cp_async_wait_all();
                 __syncthreads();
             }
             const unsigned e = min(b1, c1);
             for (unsigned i = b0 + tx; i < e; i += SEG_THREADS) {
-                const uint2 r = S.rec[i - c0];
-                const unsigned wis = r.y & (HR_BIN_SEG - 1u), op = (r.y >> 16) & 0xFFu, tid = r.x;
+                unsigned wis, op, tid;
+                if (PACK4) {
+                    const unsigned x = rec4[i - c0];
+                    wis = x & (HR_BIN_SEG - 1u);
+                    op = (x >> HR_BIN_SEG_SHIFT) & 3u;
+                    tid = x >> PACK4_TID_SHIFT;
+                } else {
+                    const uint2 r = S.rec[i - c0];
+                    wis = r.y & (HR_BIN_SEG - 1u);
+                    op = (r.y >> 16) & 0xFFu;
+                    tid = r.x;
+                }
                 unsigned long long o = S.sh[wis];
                 unsigned raced = 0;
                 unsigned long long nv =
@@ -679,6 +689,97 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
             b0 = e;
         }
     }
+    *n_cas_out = n_cas;
+    *n_retry_out = n_retry;
+    *err_out = err;
+}
+
+// POW2: the region's block size and warp size are powers of two (hr_bin::pow2),
+// and the FSM step takes its bit-operation form
+template <bool POW2>
+__global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
+    hr_bin_segments(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SegSmem& S = *reinterpret_cast<SegSmem*>(smem_raw);
+    if (!w.ctl->binned) return;
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev* rg = regions + jb.region;
+    if (*(volatile unsigned*)&rg->error) return;
+    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
+    const bool pack4 = w.ctl->bin_pack4 != 0;
+    const bool fresh = w.ctl->fresh != 0;  // nothing in the shadow is live: zeros instead of a read
+    const unsigned seg = blockIdx.x, tx = threadIdx.x;
+    // this segment's accesses: [row[0], the next row's first entry); a wave's
+    // accesses end where the next wave's first part begins
+    const unsigned* row = w.bin.table + (size_t)seg * P;
+    const unsigned r_end = seg + 1 < w.bin.n_seg ? row[P] : w.ctl->bin_total;
+    for (unsigned p = tx; p < P; p += SEG_THREADS) {
+        const unsigned wv = w.bin.part_wave[p];
+        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.wave[wv].x = p + 1 == P ? r_end : row[p + 1];
+    }
+    for (unsigned i = tx; i < W; i += SEG_THREADS) {
+        const unsigned long long key = w.wave_key[jb.wave_begin + i];
+        const unsigned kern = (unsigned)(key >> 32);
+        S.wave[i].y = ((unsigned)key & 0xFFFF0000u) | (w.bin.clear[i] ? 0x8000u : 0u) | ((kern & 7u) << 8) |
+                      ((unsigned)key & 0xFFu);
+        S.kern[i] = kern;
+    }
+    for (unsigned i = tx; i < 2048 / 4; i += SEG_THREADS)
+        reinterpret_cast<unsigned*>(S.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
+    if (tx == 0) {
+        S.r0 = row[0];
+        S.n_races = 0;
+    }
+    const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
+    const unsigned r0 = S.r0;
+    const unsigned r1 = S.wave[W - 1].x;
+    if (r0 == r1 && !any_clear) return;  // no access and no clear: the segment is untouched
+
+    const hr_geom g = rg->geom;
+    const unsigned long long w0 = (unsigned long long)seg * HR_BIN_SEG;
+    const unsigned nws = (unsigned)min((unsigned long long)HR_BIN_SEG, rg->n_words - w0);
+    unsigned long long* shadow = rg->shadow;
+    const bool compact = g.shadow_bytes == 4;
+    if (r0 == r1) {
+        // only clears: the segment ends cleared
+        for (unsigned i = tx; i < nws; i += SEG_THREADS) {
+            if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = 0u;
+            else shadow[w0 + i] = 0ull;
+        }
+        return;
+    }
+    // the segment's shadow (segment starts are 16-byte aligned; a ragged tail by
+    // plain loads), or zeros when nothing in it is live; the first accesses come
+    // in with it
+    const unsigned CH = pack4 ? 2 * HR_BIN_CHUNK : HR_BIN_CHUNK;
+    unsigned c0 = r0, c1 = r0;  // staged accesses [c0, c1)
+    if (fresh) {
+        for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
+    } else if (!compact) {
+        for (unsigned i = tx; i < nws / 2; i += SEG_THREADS) cp_async16(&S.sh[2 * i], shadow + w0 + 2 * i);
+        if ((nws & 1u) && tx == 0) S.sh[nws - 1] = shadow[w0 + nws - 1];
+    } else {
+        unsigned* raw = reinterpret_cast<unsigned*>(S.rec);
+        const unsigned* src = reinterpret_cast<const unsigned*>(shadow) + w0;
+        for (unsigned i = tx; i < nws / 4; i += SEG_THREADS) cp_async16(&raw[4 * i], src + 4 * i);
+        if (tx < (nws & 3u)) raw[(nws & ~3u) + tx] = src[(nws & ~3u) + tx];
+        cp_async_wait_all();
+        __syncthreads();
+        for (unsigned i = tx; i < nws; i += SEG_THREADS) S.sh[i] = hr_expand32(raw[i], g);
+        __syncthreads();
+    }
+    c1 = min(r0 + CH, r1);
+    if (pack4) stage_accesses<true>(S, w, c0, c1);
+    else stage_accesses<false>(S, w, c0, c1);
+    cp_async_wait_all();
+    __syncthreads();
+
+    const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
+    unsigned n_cas = 0, n_retry = 0, err = 0;
+    const unsigned n_acc = tx == 0 ? r1 - r0 : 0u;  // every access of [r0, r1) is applied once
+    if (pack4) apply_waves<POW2, true>(S, w, rg, g, W, r0, r1, c0, c1, word_off, &n_cas, &n_retry, &err);
+    else apply_waves<POW2, false>(S, w, rg, g, W, r0, r1, c0, c1, word_off, &n_cas, &n_retry, &err);
     // write the segment back
     for (unsigned i = tx; i < nws; i += SEG_THREADS) {
         if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = hr_compress64(S.sh[i], g);
@@ -712,6 +813,370 @@ __global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
     }
 }
 
+// ------------------------------------------------------------ 5'. segments, persistent groups
+//
+// One CTA of 1024 threads per SM, cut into independent thread groups; a group
+// takes a segment (atomic ticket, so uneven segments balance), applies it like
+// hr_bin_segments and takes the next.  A group synchronises with a named
+// barrier of its own, never the whole CTA.  Two layouts:
+//   compact (ctl->bin_tbits != 0): 8 groups of 128 threads, the segment's
+//     working shadow 4 bytes per word (tid in tbits bits, wc and bc in the rest
+//     of 24, state and kernel tag on top: the compact storage form of the 8-byte
+//     value, which the checker expands for every FSM step).  Taken only when
+//     nothing in the shadow is live and every tid and clock of the check fits,
+//     so each value the FSM stores fits too.  About one thread per access of a
+//     wave of the benchmark trace.
+//   full: 4 groups of 256 threads, 8-byte working shadow.
+
+constexpr unsigned PG_THREADS = 1024;
+constexpr unsigned PG_RACES = 64;           // races a group buffers per segment
+constexpr unsigned PG_STAGE_BYTES_C = 8192; // staged accesses per group, compact layout
+constexpr unsigned PG_STAGE_BYTES_F = 16384;
+
+struct alignas(16) PGroupC {
+    unsigned sh[HR_BIN_SEG];
+    unsigned char stage[PG_STAGE_BYTES_C];
+    unsigned wend[HR_BIN_MAX_WAVES];
+    hr_race races[PG_RACES];
+    unsigned seg, n_races;
+    unsigned long long race_base;
+};
+struct alignas(16) PGroupF {
+    unsigned long long sh[HR_BIN_SEG];
+    unsigned char stage[PG_STAGE_BYTES_F];
+    unsigned wend[HR_BIN_MAX_WAVES];
+    hr_race races[PG_RACES];
+    unsigned seg, n_races;
+    unsigned long long race_base;
+};
+struct alignas(16) PCommon {
+    unsigned char tab[2048];
+    unsigned wave_y[HR_BIN_MAX_WAVES];  // bc << 16 | clear << 15 | ktag << 8 | wc
+    unsigned kern[HR_BIN_MAX_WAVES];
+    unsigned lastp[HR_BIN_MAX_WAVES];   // the last part of each wave (parts are in trace order)
+    unsigned red[3][PG_THREADS / 32];
+    int any_clear;
+};
+constexpr size_t PG_GROUPS_BYTES = sizeof(PGroupC) * 8 > sizeof(PGroupF) * 4 ? sizeof(PGroupC) * 8 : sizeof(PGroupF) * 4;
+constexpr size_t PG_SMEM = sizeof(PCommon) + PG_GROUPS_BYTES;
+static_assert(PG_SMEM <= 227 * 1024, "the persistent segment CTA fits in shared memory");
+// every group (and its 8-byte fields, its 16-byte cp.async destinations) starts 16-byte aligned
+static_assert(sizeof(PCommon) % 16 == 0 && sizeof(PGroupC) % 16 == 0 && sizeof(PGroupF) % 16 == 0,
+              "16-byte aligned group layouts");
+static_assert(offsetof(PGroupF, stage) % 16 == 0 && offsetof(PGroupC, stage) % 16 == 0 &&
+                  offsetof(PGroupF, race_base) % 8 == 0 && offsetof(PGroupC, race_base) % 8 == 0,
+              "aligned group fields");
+static_assert(PG_STAGE_BYTES_C >= HR_BIN_SEG * 4 / 2, "staging sizes");
+
+__device__ __forceinline__ void group_sync(unsigned id, unsigned n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// working value (4 bytes) <-> 8-byte layout, tid in tb bits
+__device__ __forceinline__ unsigned long long pg_expand(unsigned x, const hr_geom& gw) { return hr_expand32(x, gw); }
+__device__ __forceinline__ unsigned pg_compress(unsigned long long v, const hr_geom& gw) { return hr_compress64(v, gw); }
+
+// The FSM step of Algorithm 1 on the 4-byte working form (the compact storage
+// form with tid width tb, hr_expand32): the same transition as
+// hr_fsm_step_pow2 on the expanded value, with 32-bit operations only.  wbits
+// is the wave's kernel tag, bc and wc placed where the form keeps them; mbc and
+// mwc mask the bc and wc fields; keep_w and keep_b keep the tid bits of a
+// warp's and of a block's first thread (~(warp_size - 1), ~(block_dim - 1)).
+__device__ __forceinline__ unsigned compact_step(unsigned x, unsigned tid, unsigned op, unsigned wbits, unsigned mbc,
+                                                 unsigned mwc, unsigned tidmask, unsigned bd_shift,
+                                                 unsigned ws_shift, unsigned keep_w, unsigned keep_b,
+                                                 const unsigned char* tab, unsigned* raced)
+{
+    const unsigned d = x ^ wbits;
+    unsigned os = x >> 27;
+    if (d & 0x07000000u) os = HR_STATE_INIT;  // another kernel's value (or INIT already)
+    const unsigned xt = (x & tidmask) ^ tid;
+    const unsigned trel = xt == 0u ? HR_TREL_SAME : (xt >> bd_shift) ? HR_TREL_GRID
+                        : (xt >> ws_shift) ? HR_TREL_BLOCK : HR_TREL_WARP;
+    const unsigned srel = (d & mbc) ? HR_SREL_BLOCK : ((d & mwc) ? HR_SREL_WARP : HR_SREL_UNSYNC);
+    const unsigned e = tab[(os << 6) | (op << 4) | (trel << 2) | srel];
+    const unsigned ns = e & 31u, lvl = e >> 5;
+    unsigned nx = (ns << 27) | (wbits & 0x07000000u);
+    if (lvl >= HR_LVL_THREAD && lvl <= HR_LVL_BLOCK)
+        nx |= (tid & (lvl == HR_LVL_THREAD ? ~0u : (lvl == HR_LVL_WARP ? keep_w : keep_b))) |
+              (wbits & (lvl == HR_LVL_BLOCK ? mbc : (mbc | mwc)));
+    if (ns == HR_STATE_RACE && os != HR_STATE_RACE) *raced = 1u + os;
+    return nx;
+}
+
+template <bool COMPACT, typename T>
+__device__ __forceinline__ unsigned long long as64_store(T v, const hr_geom& gw)
+{
+    if constexpr (COMPACT) return hr_expand32((unsigned)v, gw);
+    else return (unsigned long long)v;
+}
+
+template <bool POW2, bool COMPACT, bool PACK4>
+__device__ __forceinline__ void pg_run(unsigned char* gbase, PCommon& C, const hr_work& w, hr_region_dev* rg,
+                                       const hr_geom& g, unsigned W, unsigned P, unsigned gid, unsigned* cnt)
+{
+    using Grp = typename std::conditional<COMPACT, PGroupC, PGroupF>::type;
+    constexpr unsigned GT = COMPACT ? 128u : 256u;
+    constexpr unsigned STAGE = COMPACT ? PG_STAGE_BYTES_C : PG_STAGE_BYTES_F;
+    constexpr unsigned CH = STAGE / (PACK4 ? 4u : 8u);  // accesses staged at a time
+    Grp& G = reinterpret_cast<Grp*>(gbase)[gid];
+    const unsigned bar = gid + 1, t = threadIdx.x - gid * GT;
+    hr_geom gw = g;  // the working form's packing (compact layout)
+    gw.tid_bits = w.ctl->bin_tbits;
+    const unsigned tb = gw.tid_bits, wcb = (24u - tb) >> 1;
+    const unsigned tidmask = tb ? (1u << tb) - 1u : 0u;
+    const unsigned mwc = ((1u << wcb) - 1u) << tb, mbc = 0x00FFFFFFu & ~((1u << (tb + wcb)) - 1u);
+    const unsigned keep_w = POW2 ? ~((1u << min(g.ws_shift, g.bd_shift)) - 1u) : 0u;
+    const unsigned keep_b = POW2 ? ~((1u << g.bd_shift) - 1u) : 0u;
+    const bool fresh = w.ctl->fresh != 0;
+    const bool store4 = g.shadow_bytes == 4;
+    const unsigned cap = w.cas_cap;
+    const unsigned ring_region = rg->region;
+    const unsigned long long word_lo = hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull;
+    unsigned long long* shadow = rg->shadow;
+    const unsigned n_seg = w.bin.n_seg;
+    unsigned n_acc = 0, n_cas = 0, n_retry = 0, err = 0;
+    if (t == 0) G.n_races = 0;
+    for (;;) {
+        if (t == 0) G.seg = atomicAdd(&w.ctl->seg_ticket, 1u);
+        group_sync(bar, GT);
+        const unsigned seg = G.seg;
+        if (seg >= n_seg) break;
+        // the segment's wave ends: a wave's accesses end where its last part's do
+        const unsigned* row = w.bin.table + (size_t)seg * P;
+        for (unsigned wv = t; wv < W; wv += GT) {
+            const unsigned lp = C.lastp[wv];
+            G.wend[wv] = lp + 1 < P ? row[lp + 1] : (seg + 1 < n_seg ? row[P] : w.ctl->bin_total);
+        }
+        const unsigned r0 = row[0];
+        group_sync(bar, GT);
+        const unsigned r1 = G.wend[W - 1];
+        const unsigned long long w0 = (unsigned long long)seg * HR_BIN_SEG;
+        const unsigned nws = (unsigned)min((unsigned long long)HR_BIN_SEG, rg->n_words - w0);
+        if (r0 == r1) {
+            if (C.any_clear) {  // only clears: the segment ends cleared
+                for (unsigned i = t; i < nws; i += GT) {
+                    if (store4) reinterpret_cast<unsigned*>(shadow)[w0 + i] = 0u;
+                    else shadow[w0 + i] = 0ull;
+                }
+            }
+            group_sync(bar, GT);  // G.seg and G.wend are reused
+            continue;
+        }
+        // the working shadow: zeros when nothing is live, else the stored values
+        if (COMPACT || fresh) {
+            for (unsigned i = t; i < HR_BIN_SEG; i += GT) G.sh[i] = 0;
+        } else if constexpr (!COMPACT) {
+            if (!store4) {
+                for (unsigned i = t; i < nws / 2; i += GT) cp_async16(&G.sh[2 * i], shadow + w0 + 2 * i);
+                if ((nws & 1u) && t == 0) G.sh[nws - 1] = shadow[w0 + nws - 1];
+            } else {
+                const unsigned* src = reinterpret_cast<const unsigned*>(shadow) + w0;
+                for (unsigned i = t; i < nws; i += GT) G.sh[i] = hr_expand32(src[i], g);
+            }
+        }
+        unsigned c0 = r0, c1 = min(r0 + CH, r1);
+        if (PACK4) {
+            unsigned* dst = reinterpret_cast<unsigned*>(G.stage);
+            const unsigned* src = reinterpret_cast<const unsigned*>(w.bin.out);
+            for (unsigned i = c0 + t; i < c1; i += GT) cp_async4(&dst[i - c0], &src[i]);
+        } else {
+            uint2* dst = reinterpret_cast<uint2*>(G.stage);
+            for (unsigned i = c0 + t; i < c1; i += GT) cp_async8(&dst[i - c0], &w.bin.out[i]);
+        }
+        cp_async_wait_all();
+        group_sync(bar, GT);
+        n_acc += t == 0 ? r1 - r0 : 0u;
+        unsigned b0 = r0;
+        for (unsigned gwv = 0; gwv < W; ++gwv) {
+            const unsigned wy = C.wave_y[gwv];
+            if (wy & 0x8000u) {  // kernel-tag group change before this wave: the shadow starts over
+                for (unsigned i = t; i < HR_BIN_SEG; i += GT) G.sh[i] = 0;
+                group_sync(bar, GT);
+            }
+            const unsigned b1 = G.wend[gwv];
+            const unsigned bc = wy >> 16, wc = wy & 0xFFu, ktag = (wy >> 8) & 7u;
+            const unsigned wbits = (ktag << 24) | (bc << (tb + wcb)) | (wc << tb);  // compact layout only
+            while (b0 < b1) {
+                if (b0 >= c1) {  // the next accesses (every thread is done with the staged ones)
+                    c0 = b0;
+                    c1 = min(c0 + CH, r1);
+                    if (PACK4) {
+                        unsigned* dst = reinterpret_cast<unsigned*>(G.stage);
+                        const unsigned* src = reinterpret_cast<const unsigned*>(w.bin.out);
+                        for (unsigned i = c0 + t; i < c1; i += GT) cp_async4(&dst[i - c0], &src[i]);
+                    } else {
+                        uint2* dst = reinterpret_cast<uint2*>(G.stage);
+                        for (unsigned i = c0 + t; i < c1; i += GT) cp_async8(&dst[i - c0], &w.bin.out[i]);
+                    }
+                    cp_async_wait_all();
+                    group_sync(bar, GT);
+                }
+                const unsigned e = min(b1, c1);
+                for (unsigned i = b0 + t; i < e; i += GT) {
+                    unsigned wis, op, tid;
+                    if (PACK4) {
+                        const unsigned x = reinterpret_cast<const unsigned*>(G.stage)[i - c0];
+                        wis = x & (HR_BIN_SEG - 1u);
+                        op = (x >> HR_BIN_SEG_SHIFT) & 3u;
+                        tid = x >> PACK4_TID_SHIFT;
+                    } else {
+                        const uint2 r = reinterpret_cast<const uint2*>(G.stage)[i - c0];
+                        wis = r.y & (HR_BIN_SEG - 1u);
+                        op = (r.y >> 16) & 0xFFu;
+                        tid = r.x;
+                    }
+                    auto as64 = [&](auto v) -> unsigned long long {
+                        if constexpr (COMPACT) return pg_expand((unsigned)v, gw);
+                        else return (unsigned long long)v;
+                    };
+                    // one FSM step from a stored value to the value to store
+                    auto step = [&](auto stored, unsigned* raced) -> decltype(stored) {
+                        if constexpr (COMPACT && POW2) {
+                            return compact_step(stored, tid, op, wbits, mbc, mwc, tidmask, g.bd_shift, g.ws_shift,
+                                                keep_w, keep_b, C.tab, raced);
+                        } else {
+                            const unsigned long long o = as64(stored);
+                            const unsigned long long nv =
+                                POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, C.tab, raced)
+                                     : hr_fsm_step(o, tid, op, bc, wc, ktag, g, C.tab, raced);
+                            if constexpr (COMPACT) return pg_compress(nv, gw);
+                            else return nv;
+                        }
+                    };
+                    auto stored = G.sh[wis];
+                    unsigned raced = 0;
+                    auto nst = step(stored, &raced);
+                    bool done = true;
+                    if (nst != stored) {
+                        ++n_cas;
+                        auto seen = atomicCAS(&G.sh[wis], stored, nst);
+                        if (seen != stored) {
+                            // another access of this wave changed the word first: fold into
+                            // what it left, at most cap more times
+                            ++n_retry;
+                            done = false;
+                            for (unsigned tries = 0; tries < cap; ++tries) {
+                                stored = seen;
+                                raced = 0;
+                                nst = step(stored, &raced);
+                                if (nst == stored) {
+                                    done = true;
+                                    break;
+                                }
+                                ++n_cas;
+                                seen = atomicCAS(&G.sh[wis], stored, nst);
+                                if (seen == stored) {
+                                    done = true;
+                                    break;
+                                }
+                            }
+                        }
+                    }
+                    if (!done) {
+                        err = HR_ERR_CONTENTION;
+                    } else if (raced) {
+                        const unsigned k = atomicAdd(&G.n_races, 1u);
+                        const unsigned word = (unsigned)(word_lo + w0 + wis);
+                        if (k < PG_RACES) {
+                            hr_race& x = G.races[k];
+                            x.word = word;
+                            x.tid = tid;
+                            x.kernel = (uint16_t)C.kern[gwv];
+                            x.epoch = (uint16_t)bc;
+                            x.region = (uint16_t)ring_region;
+                            x.op = (uint8_t)op;
+                            x.prior = (uint8_t)(raced - 1u);
+                        } else {
+                            hr_append_race(rg->ring, rg->ring_cap, &rg->n_races, &rg->flags, word, tid, C.kern[gwv],
+                                           bc, ring_region, op, raced - 1u);
+                        }
+                    }
+                }
+                group_sync(bar, GT);
+                b0 = e;
+            }
+        }
+        // write the segment back in the region's storage form
+        for (unsigned i = t; i < nws; i += GT) {
+            const unsigned long long v = as64_store<COMPACT>(G.sh[i], gw);
+            if (store4) reinterpret_cast<unsigned*>(shadow)[w0 + i] = hr_compress64(v, g);
+            else shadow[w0 + i] = v;
+        }
+        // the buffered races: one reservation on the region's counter
+        const unsigned nr = min(G.n_races, PG_RACES);
+        if (nr) {
+            if (t == 0) G.race_base = atomicAdd(&rg->n_races, (unsigned long long)nr);
+            group_sync(bar, GT);
+            for (unsigned i = t; i < nr; i += GT) {
+                const unsigned long long slot = G.race_base + i;
+                if (slot < rg->ring_cap) rg->ring[slot] = G.races[i];
+                else atomicOr(&rg->flags, HR_FLAG_TRUNCATED);
+            }
+        }
+        group_sync(bar, GT);  // every thread is done with G before it is reused
+        if (t == 0) G.n_races = 0;
+    }
+    if (err) hr_set_error(&rg->error, err);
+    cnt[0] = n_acc;
+    cnt[1] = n_cas;
+    cnt[2] = n_retry;
+}
+
+template <bool POW2>
+__global__ void __launch_bounds__(PG_THREADS, 1)
+    hr_bin_groups(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PCommon& C = *reinterpret_cast<PCommon*>(smem_raw);
+    unsigned char* gbase = smem_raw + sizeof(PCommon);
+    if (!w.ctl->binned) return;
+    const hr_jobd jb = w.jobs[0];
+    hr_region_dev* rg = regions + jb.region;
+    if (*(volatile unsigned*)&rg->error) return;
+    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts, tx = threadIdx.x;
+    for (unsigned i = tx; i < W; i += PG_THREADS) {
+        const unsigned long long key = w.wave_key[jb.wave_begin + i];
+        const unsigned kern = (unsigned)(key >> 32);
+        C.wave_y[i] = ((unsigned)key & 0xFFFF0000u) | (w.bin.clear[i] ? 0x8000u : 0u) | ((kern & 7u) << 8) |
+                      ((unsigned)key & 0xFFu);
+        C.kern[i] = kern;
+    }
+    for (unsigned i = tx; i < 2048 / 4; i += PG_THREADS)
+        reinterpret_cast<unsigned*>(C.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
+    for (unsigned p = tx; p < P; p += PG_THREADS) {
+        const unsigned wv = w.bin.part_wave[p];
+        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) C.lastp[wv] = p;
+    }
+    const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
+    if (tx == 0) C.any_clear = any_clear;
+    __syncthreads();
+    const hr_geom g = rg->geom;
+    const bool compact = w.ctl->bin_tbits != 0, pack4 = w.ctl->bin_pack4 != 0;
+    unsigned cnt[3] = {0, 0, 0};
+    if (compact) {
+        if (pack4) pg_run<POW2, true, true>(gbase, C, w, rg, g, W, P, tx >> 7, cnt);
+        else pg_run<POW2, true, false>(gbase, C, w, rg, g, W, P, tx >> 7, cnt);
+    } else {
+        if (pack4) pg_run<POW2, false, true>(gbase, C, w, rg, g, W, P, tx >> 8, cnt);
+        else pg_run<POW2, false, false>(gbase, C, w, rg, g, W, P, tx >> 8, cnt);
+    }
+    // diagnostics: accesses, CAS attempts, retries
+    const unsigned lane = tx & 31, wid = tx >> 5;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) cnt[k] += __shfl_xor_sync(0xFFFFFFFFu, cnt[k], o);
+        if (lane == 0) C.red[k][wid] = cnt[k];
+    }
+    __syncthreads();
+    if (tx < 3) {
+        unsigned long long t = 0;
+        for (unsigned i = 0; i < PG_THREADS / 32; ++i) t += C.red[tx][i];
+        if (t) atomicAdd(&rg->counters[tx], t);
+    }
+}
+
 bool g_attrs = false;
 
 }  // namespace
@@ -728,6 +1193,8 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
         cudaFuncSetAttribute(hr_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
         cudaFuncSetAttribute(hr_bin_segments<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
         cudaFuncSetAttribute(hr_bin_segments<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
+        cudaFuncSetAttribute(hr_bin_groups<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG_SMEM);
+        cudaFuncSetAttribute(hr_bin_groups<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG_SMEM);
         g_attrs = true;
     }
     const hr_bin& b = w.bin;
@@ -740,8 +1207,20 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
     hr_bin_scan_sums<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scan<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scatter<<<b.clusters * CL, STREAM_THREADS, SCATTER_SMEM, stream>>>(d_regions, w);
-    if (b.pow2) hr_bin_segments<true><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
-    else hr_bin_segments<false><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+    static const bool old_segments = getenv("HR_BIN_SEG_KERNEL") && !strcmp(getenv("HR_BIN_SEG_KERNEL"), "old");
+    if (old_segments) {
+        if (b.pow2) hr_bin_segments<true><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+        else hr_bin_segments<false><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
+    } else {
+        static int sms = 0;
+        if (!sms) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        if (b.pow2) hr_bin_groups<true><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
+        else hr_bin_groups<false><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
+    }
     return cudaGetLastError();
 }
 

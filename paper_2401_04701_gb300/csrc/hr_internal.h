@@ -117,6 +117,14 @@ struct hr_ctl {
     unsigned long long t0_ns;  // device clock when the check's first kernel started
     unsigned bin_parts;    // binned checker: (slice, wave) parts of the trace
     unsigned bin_total;    // binned checker: accesses moved into buckets
+    unsigned fresh;        // 1: every shadow value reads as INIT for this check's first wave (the region
+                           // is new or reset, or its last record came from an older kernel and no device
+                           // view writes it), so a shadow segment need not be read
+    unsigned bin_max_tid;  // binned checker: largest thread id of an applied access
+    unsigned bin_pack4;    // binned checker: bucketed accesses are 4 bytes (tid < 2^(30 - HR_BIN_SEG_SHIFT))
+    unsigned bin_tbits;    // binned checker: 0, or the tid width of a 4-byte working shadow in shared memory
+                           // (fresh checks whose tids and clocks fit it)
+    unsigned seg_ticket;   // binned checker: next segment a thread group of the segment pass takes
 };
 
 // Scratch of the binned checker (hr_binned.cu), one per region.  The region's
@@ -143,7 +151,8 @@ struct hr_bin {
     unsigned* sums;          // [seg_cap * part_cap / HR_BIN_SCAN + 1] per scan block
     unsigned* part_wave;     // [part_cap] wave of each part (ascending)
     unsigned char* clear;    // [HR_BIN_MAX_WAVES] 1: the shadow is cleared before this wave
-    uint2* out;              // [out_cap] bucketed accesses {tid, op << 16 | word within the segment}
+    uint2* out;              // [out_cap] bucketed accesses {tid, op << 16 | word within the segment}, or
+                             // when ctl->bin_pack4 as unsigned tid << (SEG_SHIFT + 2) | op << SEG_SHIFT | word
     unsigned long long out_cap;
     unsigned n_seg;          // segments of this check's region
     unsigned seg_cap;        // segments the table holds
@@ -172,6 +181,8 @@ struct hr_work {
     unsigned cas_cap;                // CAS retries before HR_ERR_CONTENTION
     unsigned long long wait_ns;      // bound of every device-side wait
     unsigned test_flags;             // HR_TEST_* hooks (tests only)
+    unsigned views;                  // 1: a device view of the checked region exists (inline writes may
+                                     // carry kernel ordinals the region's last key does not know)
     hr_bin bin;                      // binned checker scratch (variant HR_BIN_VARIANT only)
 };
 
@@ -275,7 +286,7 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w, const hr_
 // interval size and count for a job of n records when it may use up to budget intervals
 void hr_plan_intervals(unsigned long long n, unsigned budget, unsigned* G, unsigned* n_int);
 int hr_check_grid_size(unsigned variant);
-constexpr unsigned HR_SMALL_INTERVALS = 4096;  // single traces of at most this many pre-pass intervals take the one-CTA pre-pass
+constexpr unsigned HR_SMALL_INTERVALS = 4096;  // pre-pass intervals of a single trace (the one-CTA pre-pass)
 // The binned checker's five launches (hr_binned.cu), queued after the pre-pass
 // of a single-job check; the per-wave checker queued after them finds no items
 // when they took the check.

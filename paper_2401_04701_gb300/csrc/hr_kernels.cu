@@ -102,6 +102,7 @@ __global__ void hr_scan_intervals(const JobParams<CAP> P, unsigned total_int, hr
         unsigned cnt = 0;
         if (need) {
             bool bad = false;
+#pragma unroll 8
             for (unsigned long long c = beg; c < end; c += 32) {
                 const unsigned long long p = c + lane;
                 if (p < end) {
@@ -156,9 +157,11 @@ __device__ void scan_counts_body(hr_work& w, unsigned total_int, hr_region_dev* 
     const unsigned per = (total_int + 1023) / 1024;
     const unsigned b = threadIdx.x * per, e = min(total_int, b + per);
     unsigned local = 0;
+#pragma unroll 8
     for (unsigned i = b; i < e; ++i) local += w.counts[i];
     unsigned long long total;
     unsigned run = (unsigned)block_exclusive_scan(local, &total);
+#pragma unroll 8
     for (unsigned i = b; i < e; ++i) {
         const unsigned c = w.counts[i];
         w.counts[i] = run;
@@ -181,6 +184,8 @@ __device__ void scan_counts_body(hr_work& w, unsigned total_int, hr_region_dev* 
         w.ctl->total_items = 0;
         w.ctl->n_stages = 0;
         w.ctl->binned = 0;
+        w.ctl->fresh = 0;
+        w.ctl->bin_max_tid = 0;
         w.ctl->n_waves = over ? 0u : (unsigned)total;
     }
 }
@@ -208,6 +213,7 @@ __global__ void hr_write_waves(const JobParams<CAP> P, unsigned total_int, hr_wo
         const unsigned next = (i + 1 < total_int) ? w.counts[i + 1] : n_waves;
         unsigned off = w.counts[i];
         if (off == next) continue;  // no boundary in this interval
+#pragma unroll 8
         for (unsigned long long c = beg; c < end; c += 32) {
             const unsigned long long p = c + lane;
             bool is_b = false;
@@ -293,6 +299,10 @@ __device__ void stages_one_job(hr_work& w, hr_region_dev* regions)
         if (nw > 0 && w.wave_key[jb.wave_begin] < rg.last_key) hr_set_error(&rg.error, HR_ERR_ORDER);
         w.ctl->n_stages = n_st;
         w.ctl->total_items = failed ? 0u : (unsigned)tot;
+        // a zero shadow (new or reset region), one cleared before the first wave
+        // (used == 2), or one last written by an older kernel: nothing in it is live
+        w.ctl->fresh = !failed && nw > 0 && !w.views &&
+                       (rg.used != 1 || (w.wave_key[jb.wave_begin] >> 32) > (rg.last_key >> 32));
         if (!failed && nw > 0) {
             rg.last_key = w.wave_key[jb.wave_begin + nw - 1];
             rg.used = 1;
@@ -370,6 +380,53 @@ __global__ void __launch_bounds__(1024) hr_build_stages(hr_work w, hr_region_dev
         stages_many_jobs(w, regions);
 }
 
+// The wave boundaries of records [beg, end) of a trace (a boundary is a
+// position p whose key differs from the key at p - 1; p = 0 is one), found by
+// one warp without reading every record: from the key k at the current
+// position, a 32-way search (each lane probes one position per round, the
+// range shrinks 32-fold) finds the first later position whose key differs, so
+// a boundary costs about log32(end - beg) rounds of one load per lane.  emit(p,
+// key) is called by every lane for each boundary, in ascending order.  Returns
+// false if a boundary's key is below the key before it (the trace is not wave
+// sorted there); records that differ from their wave's key without forming a
+// boundary are caught by the checkers, which compare every record with its
+// wave's key.
+template <class Emit>
+__device__ __forceinline__ bool interval_boundaries(const hr_record* t, unsigned long long kb, unsigned long long beg,
+                                                    unsigned long long end, Emit emit)
+{
+    const unsigned lane = threadIdx.x & 31;
+    if (beg >= end) return true;
+    bool ordered = true;
+    unsigned long long lo = beg, k;
+    if (beg == 0) {
+        k = key_at(t, 0, kb);
+        emit(0ull, k);
+        lo = 1;
+    } else {
+        k = key_at(t, beg - 1, kb);
+    }
+    const unsigned long long k_end = key_at(t, end - 1, kb);
+    while (lo < end && k_end != k) {
+        // the first position in [lo, end) whose key differs from k: the key at h - 1 differs
+        unsigned long long l = lo, h = end;
+        while (h - l > 1) {
+            const unsigned long long step = (h - l + 31) / 32;
+            const unsigned long long x = min(l + (lane + 1) * step, h) - 1;
+            const bool differs = key_at(t, x, kb) != k;
+            const unsigned j = __ffs(__ballot_sync(0xffffffffu, differs)) - 1;  // some lane differs: x(31) = h - 1
+            h = min(l + (j + 1) * step, h);
+            l = l + j * step;
+        }
+        const unsigned long long kq = key_at(t, l, kb);
+        ordered = ordered && kq > k;
+        emit(l, kq);
+        k = kq;
+        lo = l + 1;
+    }
+    return ordered;
+}
+
 // The whole pre-pass of one small trace (at most HR_SMALL_INTERVALS intervals)
 // in one CTA: the four kernels above as phases separated by block barriers, so
 // a small check costs two launches instead of five.  Phase (a) finds the
@@ -408,23 +465,10 @@ __global__ void __launch_bounds__(1024) hr_prepass_small(const JobParams<1> P, u
         const unsigned i = s_list[q];
         const unsigned long long beg = (unsigned long long)i * G, end = min(n, beg + G);
         unsigned cnt = 0;
-        bool bad = false;
-#pragma unroll 8
-        for (unsigned long long c = beg; c < end; c += 32) {
-            const unsigned long long p = c + lane;
-            if (p < end) {
-                const unsigned long long k = key_at(jb.trace, p, kb);
-                if (p == 0) {
-                    cnt++;
-                } else {
-                    const unsigned long long kp = key_at(jb.trace, p - 1, kb);
-                    cnt += k != kp;
-                    bad |= k < kp;
-                }
-            }
-        }
-        if (bad) hr_set_error(&regions[jb.region].error, HR_ERR_ORDER);
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const bool ordered = interval_boundaries(jb.trace, kb, beg, end, [&](unsigned long long, unsigned long long) {
+            ++cnt;
+        });
+        if (!ordered && lane == 0) hr_set_error(&regions[jb.region].error, HR_ERR_ORDER);
         if (lane == 0) w.counts[i] = cnt;
     }
     __syncthreads();
@@ -436,27 +480,14 @@ __global__ void __launch_bounds__(1024) hr_prepass_small(const JobParams<1> P, u
     for (unsigned q = warp; q < n_need && n_waves; q += blockDim.x >> 5) {
         const unsigned i = s_list[q];
         const unsigned long long beg = (unsigned long long)i * G, end = min(n, beg + G);
-        const unsigned next = (i + 1 < total_int) ? w.counts[i + 1] : n_waves;
         unsigned off = w.counts[i];
-        if (off == next) continue;
-        for (unsigned long long c = beg; c < end; c += 32) {
-            const unsigned long long p = c + lane;
-            bool is_b = false;
-            unsigned long long k = 0;
-            if (p < end) {
-                k = key_at(jb.trace, p, kb);
-                is_b = (p == 0) || k != key_at(jb.trace, p - 1, kb);
+        interval_boundaries(jb.trace, kb, beg, end, [&](unsigned long long p, unsigned long long k) {
+            if (lane == 0 && off < n_waves) {
+                w.wave_start[off] = p;
+                w.wave_key[off] = k;
             }
-            const unsigned mask = __ballot_sync(0xffffffffu, is_b);
-            if (is_b) {
-                const unsigned slot = off + __popc(mask & ((1u << lane) - 1u));
-                if (slot < n_waves) {
-                    w.wave_start[slot] = p;
-                    w.wave_key[slot] = k;
-                }
-            }
-            off += __popc(mask);
-        }
+            ++off;
+        });
     }
     __syncthreads();
     // (e)
@@ -944,11 +975,12 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 bool a = in && op <= HR_A;
                 // selective monitoring: unmonitored accesses are skipped, a word window
                 // maps words to shadow indices
-                unsigned widx = v.x;
+                // (a symmetric group folds the access onto its representative: tidf, widx)
+                unsigned widx = v.x, tidf = v.y;
                 bool mon = true;
                 if (filtering && a && same_wave) {
                     unsigned long long ix = v.x;
-                    mon = hr_monitored(filt, g, v.y, v.x, &ix);
+                    mon = hr_monitored(filt, g, &tidf, v.x, &ix);
                     widx = (unsigned)ix;
                 }
                 if (in) {
@@ -959,40 +991,40 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                         err = HR_ERR_RANGE;
                 }
                 a = a && same_wave && mon && widx < n_words;
-                if (a && !hr_fits(v.y, bc, wc, g)) {
+                if (a && !hr_fits(tidf, bc, wc, g)) {
                     err = HR_ERR_CLOCK_OVERFLOW;  // tid, bc or wc wider than the shadow packing
                     a = false;
                 }
                 act[k] = a;
                 word[k] = widx;
-                tidv[k] = v.y;
+                tidv[k] = tidf;
                 opv[k] = op;
                 grp[k] = 1u << lane;
                 if (AGG && !every) {
                     const unsigned am = __ballot_sync(0xffffffffu, a);
-                    const unsigned w1 = __shfl_up_sync(0xffffffffu, v.x, 1);
-                    const unsigned w2 = __shfl_up_sync(0xffffffffu, v.x, 2);
-                    const unsigned t1 = __shfl_up_sync(0xffffffffu, v.y, 1);
-                    const unsigned t2 = __shfl_up_sync(0xffffffffu, v.y, 2);
+                    const unsigned w1 = __shfl_up_sync(0xffffffffu, widx, 1);
+                    const unsigned w2 = __shfl_up_sync(0xffffffffu, widx, 2);
+                    const unsigned t1 = __shfl_up_sync(0xffffffffu, tidf, 1);
+                    const unsigned t2 = __shfl_up_sync(0xffffffffu, tidf, 2);
                     const unsigned o1 = __shfl_up_sync(0xffffffffu, op, 1);
                     const unsigned o2 = __shfl_up_sync(0xffffffffu, op, 2);
                     const bool a1 = lane >= 1 && ((am >> (lane - 1)) & 1u);
                     const bool a2 = lane >= 2 && ((am >> (lane - 2)) & 1u);
                     // an exact repeat (same word, thread, op, wave) of an access a lower
                     // lane applies adds nothing to the summary: drop it
-                    const bool dup = a && ((a1 && w1 == v.x && t1 == v.y && o1 == op) ||
-                                           (a2 && w2 == v.x && t2 == v.y && o2 == op));
+                    const bool dup = a && ((a1 && w1 == widx && t1 == tidf && o1 == op) ||
+                                           (a2 && w2 == widx && t2 == tidf && o2 == op));
                     if (dup) {
                         a = false;
                         act[k] = false;
                         c_merged++;
                     }
                     // other same-word lanes nearby: group them and let the lowest lane fold
-                    const bool near = a && ((a1 && w1 == v.x) || (a2 && w2 == v.x));
+                    const bool near = a && ((a1 && w1 == widx) || (a2 && w2 == widx));
                     if (__any_sync(0xffffffffu, near)) {
-                        my_acc[k * 32 + lane] = Acc{v.y, op};
+                        my_acc[k * 32 + lane] = Acc{tidf, op};
                         const unsigned am2 = __ballot_sync(0xffffffffu, a);
-                        const unsigned m = __match_any_sync(0xffffffffu, a ? v.x : 0xFFFFFFFFu) & am2;
+                        const unsigned m = __match_any_sync(0xffffffffu, a ? widx : 0xFFFFFFFFu) & am2;
                         if (a) {
                             grp[k] = m;
                             if ((unsigned)(__ffs(m) - 1) != lane) {
@@ -1227,7 +1259,7 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
         JobParams<1> P;
         P.n = 1;
         P.job[0] = jobs[0];
-        if (total_int <= HR_SMALL_INTERVALS) {  // a small trace: the whole pre-pass in one CTA
+        if (total_int <= HR_SMALL_INTERVALS) {  // the whole pre-pass in one CTA
             hr_prepass_small<<<1, 1024, 0, stream>>>(P, total_int, w, d_regions);
             prepass_launches = 1;
         } else {

@@ -120,7 +120,7 @@ extern "C" hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n
         job.trace = d_trace;
         job.n = n;
         job.region = 0;  // the region array is the single struct above
-        hr_plan_intervals(n, HR_MAX_INTERVALS, &job.G, &job.n_int);
+        hr_plan_intervals(n, HR_SMALL_INTERVALS, &job.G, &job.n_int);
         e = hr_launch_jobs(region, w, &job, 1, base + OFF_TABLE, 0u, s, nullptr);
     }
     if (e == cudaSuccess) {

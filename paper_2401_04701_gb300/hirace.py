@@ -45,7 +45,8 @@ class HrGeom(ctypes.Structure):
 class HrFilter(ctypes.Structure):
     """Mirror of hr_filter (include/hirace.h): selective monitoring."""
     _fields_ = [("word_lo", ctypes.c_uint64), ("word_hi", ctypes.c_uint64), ("block_lo", ctypes.c_uint32),
-                ("block_hi", ctypes.c_uint32), ("lane_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("block_hi", ctypes.c_uint32), ("lane_mask", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("sym_lo", ctypes.c_uint32), ("sym_hi", ctypes.c_uint32), ("sym_stride", ctypes.c_uint64)]
 
 
 class HrJob(ctypes.Structure):
@@ -61,7 +62,7 @@ class HrView(ctypes.Structure):
                 ("kernel", ctypes.c_uint32), ("region", ctypes.c_uint32), ("filter", HrFilter)]
 
 
-assert ctypes.sizeof(HrView) == 152
+assert ctypes.sizeof(HrView) == 168
 
 
 class HiRaceError(RuntimeError):
@@ -332,10 +333,12 @@ class Checker:
         return v
 
     def set_filter(self, region: int, word_lo: int = 0, word_hi: int = 0, block_lo: int = 0, block_hi: int = 0,
-                   lane_mask: int = 0xFFFFFFFF, stream=None):
+                   lane_mask: int = 0xFFFFFFFF, sym_lo: int = 0, sym_hi: int = 0, sym_stride: int = 0, stream=None):
         """Monitor only words [word_lo, word_hi) (word_hi 0: all), blocks
-        [block_lo, block_hi) (block_hi 0: all) and the lanes in lane_mask."""
-        f = HrFilter(word_lo, word_hi, block_lo, block_hi, lane_mask, 0)
+        [block_lo, block_hi) (block_hi 0: all) and the lanes in lane_mask;
+        blocks [sym_lo, sym_hi) (sym_hi 0: none) form a symmetric group checked
+        through block sym_lo, member m's words shifted by m * sym_stride."""
+        f = HrFilter(word_lo, word_hi, block_lo, block_hi, lane_mask, 0, sym_lo, sym_hi, sym_stride)
         self._check(self._lib.hr_set_filter(self._ctx, region, ctypes.byref(f), _stream_handle(stream)),
                     "hr_set_filter")
 

@@ -119,7 +119,7 @@ def kernel_accesses(name, threads):
 
 class Server:
     def __init__(self, pool: TracePool, device, n_slots=64, slot_words=1 << 26, budget_bytes=64 << 30,
-                 chunk_records=1 << 22, max_inflight=2, iteration_records=1 << 26):
+                 chunk_records=1 << 22, max_inflight=2, iteration_records=1 << 26, n_kernel_streams=4):
         import torch
         self.pool = pool
         self.device = device
@@ -133,15 +133,20 @@ class Server:
                                  report_capacity=RING)
         self.ck.batch_reserve(n_slots, 1 << 18)
         hirace.load_workloads()
-        self.stream = torch.cuda.Stream(device)
+        self.stream = torch.cuda.Stream(device)           # trace batches
+        # instrumented-kernel jobs run on streams of their own, so they overlap
+        # the trace batches (and each other) on the device
+        self.kernel_streams = [torch.cuda.Stream(device) for _ in range(n_kernel_streams)]
+        self.next_kernel_stream = 0
         self.free = list(range(n_slots))
         self.used = 0
         self.queue = collections.deque()
         self.active = {}        # slot -> job dict (trace jobs with chunks left)
-        self.inflight = collections.deque()   # (event, [finishing slots])
+        self.inflight = collections.deque()   # (event, [finishing slots], is a trace iteration)
         self.results = {}
         self.t0 = None
         self.iterations = 0
+        self.overlapped = 0     # launches queued while work of the other kind was in flight
 
     # ------------------------------------------------------------- helpers
     def _now(self):
@@ -198,7 +203,7 @@ class Server:
                 import torch
                 ev = torch.cuda.Event()
                 ev.record(self.stream)
-                self.inflight.append((ev, [(slot, job)]))
+                self.inflight.append((ev, [(slot, job)], False))
                 return True
         return False
 
@@ -221,32 +226,38 @@ class Server:
                                          accesses=self.pool.accesses(req.source, length))
             else:
                 n = req.length
+                # the slot's reset is queued on the trace stream; the job's stream waits for it
                 self.ck.reconfigure(slot, kernel_words(req.source, n), 256, stream=self.stream)
+                ready = torch.cuda.Event()
+                ready.record(self.stream)
+                if any(e[2] for e in self.inflight):
+                    self.overlapped += 1
+                ks = self.kernel_streams[self.next_kernel_stream]
+                self.next_kernel_stream = (self.next_kernel_stream + 1) % len(self.kernel_streams)
+                ks.wait_event(ready)
                 view = self.ck.device_view(slot)
                 g = torch.Generator(device=self.device).manual_seed(req.seed)
-                with torch.cuda.stream(self.stream):
+                with torch.cuda.stream(ks):
                     if req.source == "stencil":
                         a = torch.rand(n, device=self.device, generator=g)
                         bufs = (a, torch.empty_like(a))
-                        hirace.run_stencil(view, bufs[0], bufs[1], racy_stride=(req.seed % 3) * 97,
-                                           stream=self.stream)
+                        hirace.run_stencil(view, bufs[0], bufs[1], racy_stride=(req.seed % 3) * 97, stream=ks)
                     elif req.source == "histogram":
                         k = torch.randint(0, 4096, (n,), device=self.device, dtype=torch.int32, generator=g)
                         bufs = (k, torch.zeros(4096, dtype=torch.int32, device=self.device))
-                        hirace.run_histogram(view, bufs[0], bufs[1], racy_stride=(req.seed % 3) * 101,
-                                             stream=self.stream)
+                        hirace.run_histogram(view, bufs[0], bufs[1], racy_stride=(req.seed % 3) * 101, stream=ks)
                     else:
                         bufs = (torch.rand(n, device=self.device, generator=g),)
-                        hirace.run_reduce(view, bufs[0], drop_level=(req.seed % 4) - 1, stream=self.stream)
+                        hirace.run_reduce(view, bufs[0], drop_level=(req.seed % 4) - 1, stream=ks)
                 ev = torch.cuda.Event()
-                ev.record(self.stream)
+                ev.record(ks)
                 job = dict(req=req, need=need, admitted=admitted, bufs=bufs,
                            accesses=kernel_accesses(req.source, n))
-                self.inflight.append((ev, [(slot, job)]))
+                self.inflight.append((ev, [(slot, job)], False))
 
     def _launch_iteration(self):
         import torch
-        if not self.active or len(self.inflight) >= self.max_inflight:
+        if not self.active or sum(1 for e in self.inflight if e[2]) >= self.max_inflight:
             return False
         batch, finishing = [], []
         # share the iteration's record budget: a lone job takes its whole remainder,
@@ -260,16 +271,21 @@ class Server:
             if b >= job["length"]:
                 finishing.append((slot, job))
                 del self.active[slot]
+        if any(not e[2] for e in self.inflight):
+            self.overlapped += 1
         self.ck.check_batch(batch, stream=self.stream)
         ev = torch.cuda.Event()
         ev.record(self.stream)
-        self.inflight.append((ev, finishing))
+        self.inflight.append((ev, finishing, True))
         self.iterations += 1
         return True
 
     def _poll(self):
-        while self.inflight and self.inflight[0][0].query():
-            _, finished = self.inflight.popleft()
+        # entries finish out of order (kernel jobs run on their own streams)
+        done = [e for e in self.inflight if e[0].query()]
+        for e in done:
+            self.inflight.remove(e)
+            finished = e[1]
             t = self._now()
             for slot, job in finished:
                 races, status, n_total, _ = self.ck.report(slot)

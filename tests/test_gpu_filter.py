@@ -106,3 +106,94 @@ def test_filter_validation(hr, bad):
     with hr.Checker([dict(n_words=1024, block_dim=256)]) as ck:
         with pytest.raises(hr.HiRaceError):
             ck.set_filter(0, **bad)
+
+
+# ---------------------------------------------------------------------------
+# Symmetric work groups: members folded onto a representative block
+# ---------------------------------------------------------------------------
+
+def fold_trace(trace, block_dim, sym_lo, sym_hi, stride, word_lo=0, word_hi=0):
+    """The accesses the checker applies under a symmetric group, written out:
+    an access of thread t of block sym_lo + m (0 < m < sym_hi - sym_lo) to word
+    w becomes thread t - m * block_dim's access to w - m * stride (dropped if
+    w < m * stride), then the word window keeps [word_lo, word_hi).  Barrier
+    records are dropped (they carry only clocks, which every record has)."""
+    acc = trace[trace["op"] <= tg.OP_A].copy()
+    tid = acc["tid"].astype(np.int64)
+    w = acc["word"].astype(np.int64)
+    m = tid // block_dim - sym_lo
+    member = (m > 0) & (tid // block_dim < sym_hi)
+    shift = np.where(member, m * stride, 0)
+    keep = w >= shift
+    w = w - shift
+    tid = tid - np.where(member, m * block_dim, 0)
+    if word_hi:
+        keep &= (w >= word_lo) & (w < word_hi)
+    out = acc[keep]
+    out["word"] = w[keep]
+    out["tid"] = tid[keep]
+    return out
+
+
+def symmetric_program(rng, n_members, block_dim, stride, n_acc=3000):
+    """One block's random program (reads, writes, atomics on `stride` words,
+    a few barriers) run by n_members blocks, member b on words shifted up by
+    b * stride: (trace, the representative block's trace alone)."""
+    from tests import _cases as C
+    base = C.random_program(rng, n_threads=block_dim, block_dim=block_dim, n_words=stride, n_acc=n_acc,
+                            n_st=3, n_sw=2, n_kernels=1)[0]
+    progs = {}
+    for b in range(n_members):
+        for t, ev in base.items():
+            progs[b * block_dim + t] = [(e[0], e[1] + b * stride) + tuple(e[2:]) if e[0] in ("R", "W", "A") else e
+                                        for e in ev]
+    return tg.build_trace([progs]), tg.build_trace([base])
+
+
+@pytest.mark.parametrize("variant", ["plain", "aggregated", "binned"])
+def test_symmetric_group_equals_its_representative(oracle_mod, hr, variant):
+    """Exactly symmetric members: the folded check on a shadow of one member's
+    words reports the representative block's races (the same races every
+    member has, Sec. IV-A's representative tracking), and equals the oracle
+    on the folded trace."""
+    rng = np.random.default_rng(31)
+    bd, stride, G = 64, 97, 12
+    tr, rep = symmetric_program(rng, G, bd, stride)
+    want_rep = oracle_mod.race_keys(oracle_mod.bruteforce(rep, bd, 32))
+    assert want_rep
+    folded = fold_trace(tr, bd, 0, G, stride, 0, stride)
+    assert oracle_mod.race_keys(oracle_mod.bruteforce_parallel(folded, bd, stride, threads=1)) == want_rep
+    with hr.Checker([dict(n_words=stride, block_dim=bd)], report_capacity=1 << 16) as ck:
+        if variant == "binned":
+            ck.set_variant(hr.binned_variant())
+        ck.set_filter(0, word_lo=0, word_hi=stride, sym_lo=0, sym_hi=G, sym_stride=stride)
+        ck.check_trace(0, to_dev(tr), aggregate=variant == "aggregated")
+        races, status, n_total, _ = ck.report(0)
+    assert status == hr.HR_OK and hr.race_keys(races) == want_rep and n_total == len(want_rep)
+
+
+@pytest.mark.parametrize("variant", ["plain", "aggregated", "binned"])
+def test_symmetric_group_on_global_mix(oracle_mod, hr, variant):
+    """Members that are not symmetric (the global mix: random words shared by
+    all blocks): the checker applies exactly the folded accesses, with a word
+    window, blocks outside the group unchanged."""
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 14), inject=True, n_blocks=16)
+    f = dict(sym_lo=3, sym_hi=11, sym_stride=65536, word_lo=65536, word_hi=65536 * 9)
+    folded = fold_trace(tr, 256, 3, 11, 65536, 65536, 65536 * 9)
+    want = oracle_mod.race_keys(oracle_mod.bruteforce_parallel(folded, 256, info["n_words"], threads=1))
+    assert want
+    with hr.Checker([dict(n_words=65536 * 8, block_dim=256)], report_capacity=1 << 20) as ck:
+        if variant == "binned":
+            ck.set_variant(hr.binned_variant())
+        ck.set_filter(0, **f)
+        ck.check_trace(0, to_dev(tr), aggregate=variant == "aggregated")
+        races, status, n_total, _ = ck.report(0)
+    assert status == hr.HR_OK and hr.race_keys(races) == want and n_total == len(want)
+
+
+def test_symmetric_group_validation(hr):
+    with hr.Checker([dict(n_words=1024, block_dim=256)]) as ck:
+        with pytest.raises(hr.HiRaceError):
+            ck.set_filter(0, sym_lo=5, sym_hi=5)
+        with pytest.raises(hr.HiRaceError):
+            ck.set_filter(0, sym_lo=6, sym_hi=2)

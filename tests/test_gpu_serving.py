@@ -50,6 +50,37 @@ def test_alone_equals_mix(oracle_mod, env):
             assert m.keys() == want, r
 
 
+def test_kernel_jobs_overlap_trace_batches(oracle_mod, env):
+    """Instrumented-kernel jobs run on streams of their own: in a mix where
+    kernel jobs and trace chunks arrive together, launches of one kind are
+    queued while the other kind is in flight, and every result is still the
+    one the request gets alone (kernels) or the oracle's (traces)."""
+    import torch
+    serving, pool = env
+    dev = torch.device("cuda", 0)
+    R = serving.Request
+    reqs = []
+    for i in range(24):
+        if i % 2:
+            reqs.append(R(i, 0.0005 * i, "kernel", serving.KERNELS[i % 3], 256 * (64 + 32 * i), 1000 + i))
+        else:
+            reqs.append(R(i, 0.0005 * i, "trace", ("tree", "global", "graph")[i % 3], 150_000 + 9_000 * i, i))
+    srv = serving.Server(pool, dev, n_slots=12, slot_words=1 << 22, chunk_records=1 << 15,
+                         iteration_records=1 << 16)
+    mix = srv.run(reqs)
+    assert srv.overlapped > 0
+    alone = serving.Server(pool, dev, n_slots=2, slot_words=1 << 22, chunk_records=1 << 15)
+    for r in reqs:
+        alone.results = {}
+        got = alone.run([R(r.rid, 0.0, r.kind, r.source, r.length, r.seed)], warm=False)[r.rid]
+        assert got.status == mix[r.rid].status == 0, r
+        assert got.keys() == mix[r.rid].keys() and got.n_races == mix[r.rid].n_races, r
+        if r.kind == "trace":
+            e = pool.entries[r.source]
+            want = oracle_mod.race_keys(oracle_mod.bruteforce(e["host"][: min(r.length, e["n"])], e["block_dim"]))
+            assert mix[r.rid].keys() == want, r
+
+
 def test_failures_stay_with_their_request(oracle_mod, env):
     """Host-side fault injection in a served mix: malformed traces end with their
     own error status, a request too large for any slot is refused at once, a
