@@ -51,7 +51,7 @@ ALG_BYTES_PER_ACCESS_COMPACT = 24  # 16 B record + 4 B shadow read + 4 B shadow 
 
 KERNEL_SOURCES = ("paper_2401_04701_gb300/csrc/hr_kernels.cu", "paper_2401_04701_gb300/csrc/hr_binned.cu",
                   "paper_2401_04701_gb300/csrc/hr_internal.h", "include/hirace_device.cuh")
-BINNED_KERNELS = "hr_bin_count, hr_bin_scan_sums, hr_bin_scan, hr_bin_scatter, hr_bin_segments"
+BINNED_KERNELS = "hr_bin_count, hr_bin_scan_sums, hr_bin_scan, hr_bin_scatter, hr_bin_groups"
 
 
 def kernel_sources_sha():

@@ -444,6 +444,51 @@ hr_status hr_check_trace_noalloc(const hr_record* d_trace, uint64_t n, uint64_t*
                                  uint32_t block_dim, uint32_t warp_size, hr_race* d_races, uint64_t race_cap,
                                  hr_result* d_result, hr_stream_t stream);
 
+/*
+ * Word-range sharding (no paper counterpart; the paper checks on one GPU).
+ * Ranks that each own a contiguous word range [bounds[r], bounds[r+1]) of a
+ * region check one trace together: an access touches only its own word's
+ * shadow value (Algorithm 1), so each rank checks the accesses to its words
+ * on its own region, in wave order.
+ *
+ * hr_shard_partition - split the n records of d_trace (device, wave-sorted,
+ * 16-byte aligned) by owner rank.  d_bounds: world + 1 device uint64 word
+ * bounds, ascending, bounds[0] = 0 (world <= HR_SHARD_MAX_WORLD).  Each access
+ * whose word w lies in [bounds[r], bounds[r+1]) is written, with word
+ * w - bounds[r], to destination r's block of d_out (device, n records, 16-byte
+ * aligned); blocks follow one another in rank order and keep trace order
+ * inside (a stable partition, so each stays wave-sorted).  Barrier records
+ * and words at or past bounds[world] are not routed.  d_counts (device,
+ * world uint64) gets each block's record count.  d_scratch: device memory of
+ * hr_shard_partition_scratch_bytes(n, world) bytes, 8-byte aligned.
+ * Asynchronous on `stream`.  HR_ERR_INVALID for bad arguments, HR_ERR_CUDA if
+ * a launch fails.
+ */
+#define HR_SHARD_MAX_WORLD 64u
+uint64_t hr_shard_partition_scratch_bytes(uint64_t n, uint32_t world);
+hr_status hr_shard_partition(const hr_record* d_trace, uint64_t n, const uint64_t* d_bounds, uint32_t world,
+                             hr_record* d_out, uint64_t* d_counts, void* d_scratch, uint64_t scratch_bytes,
+                             hr_stream_t stream);
+
+/*
+ * hr_shard_merge - merge n_chunks wave-sorted blocks of d_in (device; block c
+ * is records [d_starts[c], d_starts[c+1]), d_starts: n_chunks + 1 device
+ * uint64, d_starts[n_chunks] = n) into one wave-sorted trace in d_out (device,
+ * n records): runs of equal wave key in key order, equal keys in block order.
+ * Inside a wave any order is a valid execution order (Sec. II-B), so the
+ * result checks like the blocks' union.  d_scratch: device memory of
+ * hr_shard_merge_scratch_bytes(max_runs) bytes, 256-byte aligned, for up to
+ * max_runs runs (a run: one block's records of one wave).  *d_status (device
+ * uint32) gets 0, HR_ERR_ORDER when a block is not wave-sorted, or
+ * HR_ERR_CAPACITY when the blocks hold more than max_runs runs (the output
+ * is then incomplete).  Asynchronous on `stream`.  HR_ERR_INVALID for bad
+ * arguments, HR_ERR_CUDA if a launch fails.
+ */
+uint64_t hr_shard_merge_scratch_bytes(uint64_t max_runs);
+hr_status hr_shard_merge(const hr_record* d_in, const uint64_t* d_starts, uint32_t n_chunks, uint64_t n,
+                         hr_record* d_out, void* d_scratch, uint64_t scratch_bytes, uint64_t max_runs,
+                         uint32_t* d_status, hr_stream_t stream);
+
 /* Static text for a status code. */
 const char* hr_status_str(hr_status s);
 

@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libhirace.so")
 WORKLOADS_LIB = os.path.join(PKG, "libhirace_workloads.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hr_kernels.cu", "hr_binned.cu", "hr_api.cu", "hr_fsm.cpp", "hr_noalloc.cu"]
+SOURCES = ["hr_kernels.cu", "hr_binned.cu", "hr_api.cu", "hr_fsm.cpp", "hr_noalloc.cu", "hr_shard.cu"]
 WORKLOAD_SOURCES = ["hr_workloads.cu"]
 
 

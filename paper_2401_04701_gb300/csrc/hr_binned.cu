@@ -6,8 +6,8 @@
 // and every wave boundary drains the GPU.  This checker organises the same
 // work around the shadow instead.  The region's shadow is cut into segments of
 // HR_BIN_SEG words, each access of the trace is moved into the bucket of its
-// (segment, wave), and one CTA per segment holds that segment's shadow in
-// shared memory and applies its buckets in wave order, with a block barrier
+// (segment, wave), and a thread group holds one segment's shadow in shared
+// memory and applies its buckets in wave order, with a barrier of the group
 // between waves.
 //
 // Why this is the same computation: Algorithm 1 folds the accesses of a word
@@ -16,7 +16,7 @@
 // equal (kernel, bc, wc)) is unordered and any order of a wave's accesses is a
 // valid execution order; processing the waves in order keeps every ordered
 // pair in order.  A word's accesses all land in one segment, and the segment's
-// CTA applies its buckets in wave order, so each word sees exactly what the
+// group applies its buckets in wave order, so each word sees exactly what the
 // per-wave checker would show it.  Buckets need no stable order, so accesses
 // are appended with atomics.
 //
@@ -35,17 +35,17 @@
 //                         each access, packed to 8 bytes (tid, op, word within
 //                         the segment), goes to its bucket's next slot (cursors
 //                         in distributed shared memory: no global atomics)
-//   5. hr_bin_segments  : per segment: shadow -> shared memory, its accesses in
-//                         wave order with a shared-memory CAS per access, races
-//                         appended to the region's ring, shadow written back
+//   5. hr_bin_groups    : persistent thread groups, one segment at a time: its
+//                         shadow in shared memory (or zeros when nothing in it
+//                         is live), its accesses in wave order with a
+//                         shared-memory CAS per access, races appended to the
+//                         region's ring, the segment written back
 // A check with more than HR_BIN_MAX_WAVES waves is not binned: the flag stays
 // clear and the per-wave checker launched after these kernels does the work.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
-#include <cstdlib>
-#include <cstring>
 #include <type_traits>
 
 #include "hr_internal.h"
@@ -531,293 +531,18 @@ __global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_
     }
 }
 
-// ------------------------------------------------------------ 5. segments
-//
-// One CTA of 256 threads per segment.  The shadow and the staged accesses come
-// in with cp.async (global -> shared, no register round trip); each wave's
-// accesses are applied with a shared-memory CAS per access and a block barrier
-// between waves; races are buffered in shared memory and appended to the ring
-// with one reservation per segment.
-
-#ifndef HR_BIN_SEG_THREADS
-#define HR_BIN_SEG_THREADS 256
-#endif
-#ifndef HR_BIN_SEG_MIN_CTAS
-#define HR_BIN_SEG_MIN_CTAS 4
-#endif
-constexpr unsigned SEG_THREADS = HR_BIN_SEG_THREADS;
-constexpr unsigned SEG_RACES = 128;  // races a segment buffers (more go to the ring one by one)
-
-struct SegSmem {
-    unsigned long long sh[HR_BIN_SEG];  // the segment's shadow, 8-byte layout
-    uint2 rec[HR_BIN_CHUNK];            // staged accesses (first the compact shadow, if any)
-    // per wave: x = end of the segment's bucket; y = bc << 16 | clear << 15 | ktag << 8 | wc
-    // (clear: the shadow starts over before the wave; a wave with accesses has wc <= 255,
-    // else the count pass stopped the check with HR_ERR_CLOCK_OVERFLOW)
-    uint2 wave[HR_BIN_MAX_WAVES];
-    unsigned kern[HR_BIN_MAX_WAVES];    // rebased kernel ordinals (race records)
-    unsigned char tab[2048];            // the FSM table
-    unsigned red[3][SEG_THREADS / 32];
-    unsigned r0, n_races;
-    unsigned long long race_base;
-    hr_race races[SEG_RACES];           // this segment's races, appended to the ring once at the end
-};
-constexpr size_t SEG_SMEM = sizeof(SegSmem);
-static_assert((SEG_SMEM + 1024) * HR_BIN_SEG_MIN_CTAS <= 228 * 1024, "the segment CTAs of one SM fit its shared memory");
-static_assert(HR_BIN_CHUNK * sizeof(uint2) >= HR_BIN_SEG * 4, "the compact shadow is staged in the access area");
-
-
 __device__ __forceinline__ void cp_async4(void* dst, const void* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-// Stage the bucketed accesses [c0, c1) in shared memory (4 or 8 bytes each).
-template <bool PACK4>
-__device__ __forceinline__ void stage_accesses(SegSmem& S, const hr_work& w, unsigned c0, unsigned c1)
-{
-    if (PACK4) {
-        unsigned* dst = reinterpret_cast<unsigned*>(S.rec);
-        const unsigned* src = reinterpret_cast<const unsigned*>(w.bin.out);
-        for (unsigned i = c0 + threadIdx.x; i < c1; i += SEG_THREADS) cp_async4(&dst[i - c0], &src[i]);
-    } else {
-        for (unsigned i = c0 + threadIdx.x; i < c1; i += SEG_THREADS) cp_async8(&S.rec[i - c0], &w.bin.out[i]);
-    }
-}
-
-// The segment's accesses after its shadow is in shared memory: waves in order,
-// a shared-memory CAS per access, a block barrier between waves.  PACK4: the
-// staged accesses are in the 4-byte form.  Returns the diagnostics counts.
-template <bool POW2, bool PACK4>
-__device__ __forceinline__ void apply_waves(SegSmem& S, const hr_work& w, hr_region_dev* rg, const hr_geom& g,
-                                            unsigned W, unsigned r0, unsigned r1, unsigned c0, unsigned c1,
-                                            unsigned long long word_off, unsigned* n_cas_out, unsigned* n_retry_out,
-                                            unsigned* err_out)
-{
-    constexpr unsigned CH = PACK4 ? 2 * HR_BIN_CHUNK : HR_BIN_CHUNK;  // accesses the staging area holds
-    const unsigned tx = threadIdx.x;
-    const unsigned cap = w.cas_cap;
-    const unsigned ring_region = rg->region;
-    const unsigned* rec4 = reinterpret_cast<const unsigned*>(S.rec);
-    unsigned n_cas = 0, n_retry = 0, err = 0;
-    unsigned b0 = r0;  // the wave's bucket starts where the previous one ended
-    for (unsigned gw = 0; gw < W; ++gw) {
-        const uint2 wv = S.wave[gw];
-        if (wv.y & 0x8000u) {  // kernel-tag group change before this wave: the shadow starts over
-            for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
-            __syncthreads();
-        }
-        const unsigned b1 = wv.x;
-        const unsigned bc = wv.y >> 16, wc = wv.y & 0xFFu, ktag = (wv.y >> 8) & 7u;
-        while (b0 < b1) {
-            if (b0 >= c1) {  // stage the next accesses (every thread is done with the previous ones)
-                c0 = b0;
-                c1 = min(c0 + CH, r1);
-                stage_accesses<PACK4>(S, w, c0, c1);
-                cp_async_wait_all();
-                __syncthreads();
-            }
-            const unsigned e = min(b1, c1);
-            for (unsigned i = b0 + tx; i < e; i += SEG_THREADS) {
-                unsigned wis, op, tid;
-                if (PACK4) {
-                    const unsigned x = rec4[i - c0];
-                    wis = x & (HR_BIN_SEG - 1u);
-                    op = (x >> HR_BIN_SEG_SHIFT) & 3u;
-                    tid = x >> PACK4_TID_SHIFT;
-                } else {
-                    const uint2 r = S.rec[i - c0];
-                    wis = r.y & (HR_BIN_SEG - 1u);
-                    op = (r.y >> 16) & 0xFFu;
-                    tid = r.x;
-                }
-                unsigned long long o = S.sh[wis];
-                unsigned raced = 0;
-                unsigned long long nv =
-                    POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab, &raced)
-                         : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
-                bool done = true;
-                if (nv != o) {
-                    ++n_cas;
-                    unsigned long long seen = atomicCAS(&S.sh[wis], o, nv);
-                    if (seen != o) {
-                        // another access of this wave changed the word first: fold into
-                        // what it left, at most cap more times
-                        ++n_retry;
-                        done = false;
-                        for (unsigned tries = 0; tries < cap; ++tries) {
-                            o = seen;
-                            raced = 0;
-                            nv = POW2 ? hr_fsm_step_pow2(o, tid, op, bc, wc, ktag, g.bd_shift, g.ws_shift, S.tab,
-                                                         &raced)
-                                      : hr_fsm_step(o, tid, op, bc, wc, ktag, g, S.tab, &raced);
-                            if (nv == o) {
-                                done = true;
-                                break;
-                            }
-                            ++n_cas;
-                            seen = atomicCAS(&S.sh[wis], o, nv);
-                            if (seen == o) {
-                                done = true;
-                                break;
-                            }
-                        }
-                    }
-                }
-                if (!done) {
-                    err = HR_ERR_CONTENTION;
-                } else if (raced) {
-                    // buffered: a returning atomic on the region's race counter would hold
-                    // the whole CTA at the next barrier
-                    const unsigned k = atomicAdd(&S.n_races, 1u);
-                    if (k < SEG_RACES) {
-                        hr_race& x = S.races[k];
-                        x.word = (unsigned)(word_off + wis);
-                        x.tid = tid;
-                        x.kernel = (uint16_t)S.kern[gw];
-                        x.epoch = (uint16_t)bc;
-                        x.region = (uint16_t)ring_region;
-                        x.op = (uint8_t)op;
-                        x.prior = (uint8_t)(raced - 1u);
-                    } else {
-                        hr_append_race(rg->ring, rg->ring_cap, &rg->n_races, &rg->flags, (unsigned)(word_off + wis),
-                                       tid, S.kern[gw], bc, ring_region, op, raced - 1u);
-                    }
-                }
-            }
-            __syncthreads();
-            b0 = e;
-        }
-    }
-    *n_cas_out = n_cas;
-    *n_retry_out = n_retry;
-    *err_out = err;
-}
-
-// POW2: the region's block size and warp size are powers of two (hr_bin::pow2),
-// and the FSM step takes its bit-operation form
-template <bool POW2>
-__global__ void __launch_bounds__(SEG_THREADS, HR_BIN_SEG_MIN_CTAS)
-    hr_bin_segments(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SegSmem& S = *reinterpret_cast<SegSmem*>(smem_raw);
-    if (!w.ctl->binned) return;
-    const hr_jobd jb = w.jobs[0];
-    hr_region_dev* rg = regions + jb.region;
-    if (*(volatile unsigned*)&rg->error) return;
-    const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
-    const bool pack4 = w.ctl->bin_pack4 != 0;
-    const bool fresh = w.ctl->fresh != 0;  // nothing in the shadow is live: zeros instead of a read
-    const unsigned seg = blockIdx.x, tx = threadIdx.x;
-    // this segment's accesses: [row[0], the next row's first entry); a wave's
-    // accesses end where the next wave's first part begins
-    const unsigned* row = w.bin.table + (size_t)seg * P;
-    const unsigned r_end = seg + 1 < w.bin.n_seg ? row[P] : w.ctl->bin_total;
-    for (unsigned p = tx; p < P; p += SEG_THREADS) {
-        const unsigned wv = w.bin.part_wave[p];
-        if (p + 1 == P || w.bin.part_wave[p + 1] != wv) S.wave[wv].x = p + 1 == P ? r_end : row[p + 1];
-    }
-    for (unsigned i = tx; i < W; i += SEG_THREADS) {
-        const unsigned long long key = w.wave_key[jb.wave_begin + i];
-        const unsigned kern = (unsigned)(key >> 32);
-        S.wave[i].y = ((unsigned)key & 0xFFFF0000u) | (w.bin.clear[i] ? 0x8000u : 0u) | ((kern & 7u) << 8) |
-                      ((unsigned)key & 0xFFu);
-        S.kern[i] = kern;
-    }
-    for (unsigned i = tx; i < 2048 / 4; i += SEG_THREADS)
-        reinterpret_cast<unsigned*>(S.tab)[i] = reinterpret_cast<const unsigned*>(gtable)[i];
-    if (tx == 0) {
-        S.r0 = row[0];
-        S.n_races = 0;
-    }
-    const int any_clear = __syncthreads_or(tx < W && w.bin.clear[tx]);
-    const unsigned r0 = S.r0;
-    const unsigned r1 = S.wave[W - 1].x;
-    if (r0 == r1 && !any_clear) return;  // no access and no clear: the segment is untouched
-
-    const hr_geom g = rg->geom;
-    const unsigned long long w0 = (unsigned long long)seg * HR_BIN_SEG;
-    const unsigned nws = (unsigned)min((unsigned long long)HR_BIN_SEG, rg->n_words - w0);
-    unsigned long long* shadow = rg->shadow;
-    const bool compact = g.shadow_bytes == 4;
-    if (r0 == r1) {
-        // only clears: the segment ends cleared
-        for (unsigned i = tx; i < nws; i += SEG_THREADS) {
-            if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = 0u;
-            else shadow[w0 + i] = 0ull;
-        }
-        return;
-    }
-    // the segment's shadow (segment starts are 16-byte aligned; a ragged tail by
-    // plain loads), or zeros when nothing in it is live; the first accesses come
-    // in with it
-    const unsigned CH = pack4 ? 2 * HR_BIN_CHUNK : HR_BIN_CHUNK;
-    unsigned c0 = r0, c1 = r0;  // staged accesses [c0, c1)
-    if (fresh) {
-        for (unsigned i = tx; i < HR_BIN_SEG; i += SEG_THREADS) S.sh[i] = 0ull;
-    } else if (!compact) {
-        for (unsigned i = tx; i < nws / 2; i += SEG_THREADS) cp_async16(&S.sh[2 * i], shadow + w0 + 2 * i);
-        if ((nws & 1u) && tx == 0) S.sh[nws - 1] = shadow[w0 + nws - 1];
-    } else {
-        unsigned* raw = reinterpret_cast<unsigned*>(S.rec);
-        const unsigned* src = reinterpret_cast<const unsigned*>(shadow) + w0;
-        for (unsigned i = tx; i < nws / 4; i += SEG_THREADS) cp_async16(&raw[4 * i], src + 4 * i);
-        if (tx < (nws & 3u)) raw[(nws & ~3u) + tx] = src[(nws & ~3u) + tx];
-        cp_async_wait_all();
-        __syncthreads();
-        for (unsigned i = tx; i < nws; i += SEG_THREADS) S.sh[i] = hr_expand32(raw[i], g);
-        __syncthreads();
-    }
-    c1 = min(r0 + CH, r1);
-    if (pack4) stage_accesses<true>(S, w, c0, c1);
-    else stage_accesses<false>(S, w, c0, c1);
-    cp_async_wait_all();
-    __syncthreads();
-
-    const unsigned long long word_off = w0 + (hr_filter_active(rg->filter) ? rg->filter.word_lo : 0ull);
-    unsigned n_cas = 0, n_retry = 0, err = 0;
-    const unsigned n_acc = tx == 0 ? r1 - r0 : 0u;  // every access of [r0, r1) is applied once
-    if (pack4) apply_waves<POW2, true>(S, w, rg, g, W, r0, r1, c0, c1, word_off, &n_cas, &n_retry, &err);
-    else apply_waves<POW2, false>(S, w, rg, g, W, r0, r1, c0, c1, word_off, &n_cas, &n_retry, &err);
-    // write the segment back
-    for (unsigned i = tx; i < nws; i += SEG_THREADS) {
-        if (compact) reinterpret_cast<unsigned*>(shadow)[w0 + i] = hr_compress64(S.sh[i], g);
-        else shadow[w0 + i] = S.sh[i];
-    }
-    if (err) hr_set_error(&rg->error, err);
-    // the buffered races: one reservation on the region's counter
-    const unsigned nr = min(S.n_races, SEG_RACES);
-    if (nr) {
-        if (tx == 0) S.race_base = atomicAdd(&rg->n_races, (unsigned long long)nr);
-        __syncthreads();
-        for (unsigned i = tx; i < nr; i += SEG_THREADS) {
-            const unsigned long long slot = S.race_base + i;
-            if (slot < rg->ring_cap) rg->ring[slot] = S.races[i];
-            else atomicOr(&rg->flags, HR_FLAG_TRUNCATED);
-        }
-    }
-    // diagnostics: accesses, CAS attempts, retries
-    const unsigned lane = tx & 31, wid = tx >> 5;
-    unsigned c[3] = {n_acc, n_cas, n_retry};
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        for (int o = 16; o > 0; o >>= 1) c[k] += __shfl_xor_sync(0xFFFFFFFFu, c[k], o);
-        if (lane == 0) S.red[k][wid] = c[k];
-    }
-    __syncthreads();
-    if (tx < 3) {
-        unsigned long long t = 0;
-        for (unsigned i = 0; i < SEG_THREADS / 32; ++i) t += S.red[tx][i];
-        if (t) atomicAdd(&rg->counters[tx], t);
-    }
-}
-
-// ------------------------------------------------------------ 5'. segments, persistent groups
+// ------------------------------------------------------------ 5. segments, persistent groups
 //
 // One CTA of 1024 threads per SM, cut into independent thread groups; a group
-// takes a segment (atomic ticket, so uneven segments balance), applies it like
-// hr_bin_segments and takes the next.  A group synchronises with a named
+// takes a segment (atomic ticket, so uneven segments balance), loads (or,
+// when nothing in the shadow is live, zeroes) its working shadow, applies the
+// segment's buckets wave by wave with a shared-memory CAS per access, writes
+// the segment back and takes the next.  A group synchronises with a named
 // barrier of its own, never the whole CTA.  Two layouts:
 //   compact (ctl->bin_tbits != 0): 8 groups of 128 threads, the segment's
 //     working shadow 4 bytes per word (tid in tbits bits, wc and bc in the rest
@@ -1186,13 +911,11 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
 {
     if (!g_attrs) {
         // the shared-memory carveout at its maximum: 4 segment CTAs per SM
-        for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_segments<true>,
-                              (const void*)hr_bin_segments<false>})
+        for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_groups<true>,
+                              (const void*)hr_bin_groups<false>})
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         cudaFuncSetAttribute(hr_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)STREAM_SMEM);
         cudaFuncSetAttribute(hr_bin_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SCATTER_SMEM);
-        cudaFuncSetAttribute(hr_bin_segments<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
-        cudaFuncSetAttribute(hr_bin_segments<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SEG_SMEM);
         cudaFuncSetAttribute(hr_bin_groups<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG_SMEM);
         cudaFuncSetAttribute(hr_bin_groups<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PG_SMEM);
         g_attrs = true;
@@ -1207,20 +930,14 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
     hr_bin_scan_sums<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scan<<<scan_blocks, SCAN_THREADS, 0, stream>>>(w);
     hr_bin_scatter<<<b.clusters * CL, STREAM_THREADS, SCATTER_SMEM, stream>>>(d_regions, w);
-    static const bool old_segments = getenv("HR_BIN_SEG_KERNEL") && !strcmp(getenv("HR_BIN_SEG_KERNEL"), "old");
-    if (old_segments) {
-        if (b.pow2) hr_bin_segments<true><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
-        else hr_bin_segments<false><<<b.n_seg, SEG_THREADS, SEG_SMEM, stream>>>(d_regions, w, d_table);
-    } else {
-        static int sms = 0;
-        if (!sms) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        }
-        if (b.pow2) hr_bin_groups<true><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
-        else hr_bin_groups<false><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
+    static int sms = 0;  // one persistent segment CTA per SM
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
+    if (b.pow2) hr_bin_groups<true><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
+    else hr_bin_groups<false><<<sms, PG_THREADS, PG_SMEM, stream>>>(d_regions, w, d_table);
     return cudaGetLastError();
 }
 

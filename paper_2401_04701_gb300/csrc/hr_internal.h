@@ -142,7 +142,6 @@ constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per seg
 static_assert(HR_BIN_SEG_SHIFT >= 10 && HR_BIN_SEG_SHIFT <= 13, "the packed access keeps 16 bits for the word");
 constexpr unsigned HR_BIN_MAX_SEGS = 16384;              // larger regions take the per-wave checker
 constexpr unsigned HR_BIN_MAX_WAVES = 256;               // checks with more waves take the per-wave checker
-constexpr unsigned HR_BIN_CHUNK = HR_BIN_SEG / 2;        // bucketed accesses staged in shared memory at a time
 constexpr unsigned HR_BIN_SCAN = 4096;                   // table entries per scan block
 constexpr unsigned HR_BIN_CLUSTER = 8;                   // CTAs sharing bucket cursors in the scatter
 constexpr unsigned HR_BIN_MAX_SUB = 16;                  // count slices per cluster slice, at most

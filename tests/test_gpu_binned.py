@@ -18,7 +18,7 @@ from tests import _cases as C
 pytestmark = pytest.mark.gpu
 
 SEG = 4096          # shadow words per segment
-CHUNK = 2048        # bucket records staged in shared memory at a time
+CHUNK = 2048        # bucketed accesses a thread group stages in shared memory at a time (4-byte form)
 MAX_WAVES = 256     # waves of a check the binned checker takes
 
 
@@ -152,6 +152,30 @@ def test_buckets_longer_than_a_chunk(oracle_mod, hr):
     assert n_waves(tr) <= MAX_WAVES and len(tr) > 4 * CHUNK
     _, cnt = assert_parity(oracle_mod, hr, tr, 300, 256, 32)
     assert cnt["accesses"] == int(np.count_nonzero(tr["op"] <= tg.OP_A))
+
+
+def test_wide_tids_and_clocks(oracle_mod, hr):
+    """Thread ids of 17 bits (8-byte bucketed accesses, 4-byte working shadow),
+    of 23 bits and block clocks too wide for the 4-byte working shadow (both
+    then take the 8-byte working shadow), and a check that continues a kernel
+    (nothing fresh: the stored shadow is read)."""
+    tr, info = tg.gen_global_mix(tg.seed_for(2, 22), inject=True, n_blocks=300, tile_words=4096, epochs=2,
+                                 slots=2)
+    assert tr["tid"].max() >= 1 << 16
+    races, _ = assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"])
+    assert set(races["word"].tolist()) == set(info["injected"].tolist())
+    base = 1 << 23
+    wide = tg.build_trace([{base + t: [("W", t % 5), ("ST",), ("R", (t + 1) % 5)] for t in range(0, 512, 7)}])
+    assert_parity(oracle_mod, hr, wide, 5, 256, 32)
+    deep = tg.build_trace([{(1 << 17) + t: ([("R", t % 9)] + [("ST",)] * 40 + [("W", (t * 3) % 9)])
+                            for t in range(96)}])
+    assert_parity(oracle_mod, hr, deep, 9, 64, 32)
+    rng = np.random.default_rng(171)
+    kernels = C.random_program(rng, n_threads=600, block_dim=64, n_words=SEG + 77, n_acc=5000, n_st=3, n_sw=2,
+                               n_kernels=1)
+    tr = tg.build_trace(kernels)
+    cuts = [0, len(tr) // 3, 2 * len(tr) // 3, len(tr)]
+    assert_parity(oracle_mod, hr, tr, SEG + 77, 64, 32, chunks=cuts)
 
 
 def test_workloads(oracle_mod, hr):
