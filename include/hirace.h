@@ -270,7 +270,10 @@ hr_status hr_report(hr_ctx* ctx, uint32_t region, hr_race* host_out, uint64_t ca
                     uint32_t* flags);
 
 /* Counters of one region since init/reset: accesses applied, CAS attempts,
- * CAS retries, lanes merged by warp aggregation.  Synchronises like hr_report. */
+ * CAS retries, and accesses applied without a shadow access of their own
+ * (lanes folded by warp aggregation, exact repeats, and accesses to a word
+ * the per-wave checker has cached in a state that absorbs them).
+ * Synchronises like hr_report. */
 hr_status hr_counters(hr_ctx* ctx, uint32_t region, uint64_t out[4]);
 
 /* hr_reset - every shadow word of the region back to INIT, reports, counters

@@ -60,7 +60,7 @@ struct hr_region_dev {
     unsigned int used;            // 1: a record was processed since init/reset; 2: the shadow's
                                   // contents are unknown (cleared before the first wave)
     unsigned int region;
-    unsigned long long counters[4];  // accesses, CAS attempts, CAS retries, merged lanes
+    unsigned long long counters[4];  // accesses, CAS attempts, CAS retries, accesses without a shadow access
     hr_geom geom;
     hr_filter filter;             // monitored words, blocks, lanes (hr_set_filter)
 };
@@ -270,6 +270,10 @@ constexpr unsigned hr_variant_tile(unsigned v)
 constexpr int HR_RING = HR_RING_DEPTH;                   // tiles in flight in shared memory
 constexpr unsigned HR_TICKET_BATCH = HR_BATCH;           // tiles a producer claims per ticket
 constexpr unsigned HR_CLEAR_WORDS = 1u << 16;  // shadow words per clear item
+#ifndef HR_WORD_CACHE_ENTRIES
+#define HR_WORD_CACHE_ENTRIES 2048
+#endif
+constexpr unsigned HR_WORD_CACHE = HR_WORD_CACHE_ENTRIES;  // per-CTA cache of words whose state absorbs an op
 constexpr unsigned HR_MAX_INTERVALS = 1u << 16;      // pre-pass intervals of a single-trace check
 constexpr unsigned HR_BATCH_INTERVALS = 1u << 18;    // pre-pass intervals of a batch
 constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;

@@ -531,11 +531,23 @@ struct Shape {
     // tile-finish counters, per-warp geometry and diagnostics
     static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 +
                                     2 * HR_RING * 4 + CONS * sizeof(hr_geom) + CONS * 4 * 4 +
-                                    CONS * sizeof(hr_filter);
+                                    CONS * sizeof(hr_filter) + HR_WORD_CACHE * 8 + 16;
     static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long ld_relaxed_shared_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)));
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_shared_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.relaxed.cta.shared.u64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v));
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
@@ -648,7 +660,7 @@ struct Fold {
 };
 
 // Fold the accesses of one lane group (lanes in `grp`, in lane order) into o.
-__device__ __noinline__ Fold fold_group(unsigned long long o, unsigned grp, const Acc* acc, unsigned bc, unsigned wc,
+__device__ __forceinline__ Fold fold_group(unsigned long long o, unsigned grp, const Acc* acc, unsigned bc, unsigned wc,
                                         unsigned ktag, const hr_geom& g, const unsigned char* table)
 {
     Fold f{o, 0u, threadIdx.x & 31};
@@ -681,7 +693,7 @@ struct Retry {
 // Cold path: the first CAS lost a race (or validated a stale speculative
 // load).  Re-fold from the value it returned until a CAS sticks or the retry
 // cap is reached.
-__device__ __noinline__ Retry retry_cas(unsigned long long* shadow, unsigned word, unsigned long long seen,
+__device__ __forceinline__ Retry retry_cas(unsigned long long* shadow, unsigned word, unsigned long long seen,
                                         unsigned tid, unsigned op, unsigned grp, const Acc* acc, unsigned bc,
                                         unsigned wc, unsigned ktag, const hr_geom& g, const unsigned char* table,
                                         unsigned cap)
@@ -827,10 +839,35 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     hr_geom* s_geom = reinterpret_cast<hr_geom*>(s_fin + 2 * HR_RING);  // [HR_CONSUMERS]
     unsigned* s_cnt = reinterpret_cast<unsigned*>(s_geom + HR_CONSUMERS);  // [HR_CONSUMERS][4]
     hr_filter* s_filt = reinterpret_cast<hr_filter*>(s_cnt + 4 * HR_CONSUMERS);  // [HR_CONSUMERS]
+    // Words whose state absorbs an op for the rest of a kernel, seen by this CTA:
+    // ((region, kernel) tag << 5 | state) << 32 | word, direct-mapped by word.
+    // A grid-level state (GREAD, GATOMIC) stays itself or becomes RACE, and RACE
+    // stays RACE, so an access whose op the cached state absorbs changes
+    // nothing, whatever other CTAs did to the word since: it is applied without
+    // touching the shadow.  Entries are read and written whole (relaxed 64-bit
+    // accesses), so a reader never pairs one word with another's state.
+    unsigned long long* s_cache = reinterpret_cast<unsigned long long*>(s_filt + HR_CONSUMERS);  // [HR_WORD_CACHE]
+    unsigned* s_absorb = reinterpret_cast<unsigned*>(s_cache + HR_WORD_CACHE);  // [3]: states absorbing op
 
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
         reinterpret_cast<uint2*>(s_table)[i] = reinterpret_cast<const uint2*>(gtable)[i];
+    for (unsigned i = threadIdx.x; i < HR_WORD_CACHE; i += HR_THREADS) s_cache[i] = ~0ull;
+    if (threadIdx.x < 3) {
+        // a state absorbs op when every (thread relation, sync relation) of op
+        // leads back to it; only grid-level states and RACE are kept
+        const unsigned op = threadIdx.x;
+        unsigned m = 0;
+        for (unsigned st = 0; st < 32; ++st) {
+            bool all = true;
+            for (unsigned r = 0; r < 12 && all; ++r) {
+                const unsigned e = __ldg(gtable + ((st << 6) | (op << 4) | ((r / 3) << 2) | (r % 3)));
+                all = e != 0xFFu && (e & 31u) == st && (e >> 5) >= HR_LVL_GRID;
+            }
+            if (all) m |= 1u << st;
+        }
+        s_absorb[threadIdx.x] = m;
+    }
     if (threadIdx.x == 0) {
         for (int b = 0; b < HR_RING; ++b) {
             mbar_init(&s_full[b], 1);
@@ -884,7 +921,27 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         if (lane < 4) cnt[lane] = 0;
         __syncwarp();
     };
-
+    // The warp's part of tile `tn` (stage `stage`, bit 31: the job's last) is
+    // done: the CTA's last warp to finish the tile publishes one completion for
+    // the stage.  Counters indexed by tile number mod 2*ring never mix two
+    // tiles: a warp cannot finish tile tn+2*ring before every warp has
+    // finished tile tn.
+    auto publish = [&](unsigned tn, unsigned stage) {
+        __syncwarp();
+        if (lane == 0) {
+            const unsigned old = smem_add_acq_rel(&s_fin[tn % (2 * HR_RING)], 1u);
+            if ((old + 1u) % HR_CONSUMERS == 0) {
+                hr_stage* st = &w.stages[stage & 0x7FFFFFFFu];
+                if (stage >> 31) {
+                    // the job's last stage: the tile that completes it stamps the job's end
+                    const unsigned prev = atom_add_release(&st->done, 1u);
+                    if (prev + 1u == st[1].item_begin - st->item_begin) w.jobs[st->job].done_ns = globaltimer();
+                } else {
+                    red_release_add(&st->done, 1u);
+                }
+            }
+        }
+    };
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, region ? &region->error : &regions[0].error,
@@ -958,6 +1015,11 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             const unsigned bc = bcwc >> 16;
             const unsigned wc = bcwc & 0xFFFFu;
             const unsigned ktag = kern & 7u;
+            // the word cache's tag of this tile's (region, kernel); off when it does not fit 27 bits
+            const bool cache_on = !EVERY && t_region < 1024u && kern < (1u << 17) &&
+                                  g.report_mode != HR_REPORT_EVERY_EPOCH;
+            const unsigned ctag = (t_region << 17) | kern;
+            unsigned c_skip = 0;
             // non-absorbing reports: only the EVERY instantiation carries that path
             const bool every = EVERY && g.report_mode == HR_REPORT_EVERY_EPOCH;
             unsigned err = 0;
@@ -995,37 +1057,37 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                     err = HR_ERR_CLOCK_OVERFLOW;  // tid, bc or wc wider than the shadow packing
                     a = false;
                 }
+                if (cache_on && a) {  // a cached state that absorbs this op: nothing to do
+                    const unsigned long long ce = ld_relaxed_shared_u64(s_cache + (widx & (HR_WORD_CACHE - 1u)));
+                    const unsigned cy = (unsigned)(ce >> 32);
+                    if ((unsigned)ce == widx && (cy >> 5) == ctag && ((s_absorb[op] >> (cy & 31u)) & 1u)) {
+                        a = false;
+                        c_skip++;
+                    }
+                }
                 act[k] = a;
                 word[k] = widx;
                 tidv[k] = tidf;
                 opv[k] = op;
                 grp[k] = 1u << lane;
                 if (AGG && !every) {
+                    // lanes of this unit applying the same word
                     const unsigned am = __ballot_sync(0xffffffffu, a);
-                    const unsigned w1 = __shfl_up_sync(0xffffffffu, widx, 1);
-                    const unsigned w2 = __shfl_up_sync(0xffffffffu, widx, 2);
-                    const unsigned t1 = __shfl_up_sync(0xffffffffu, tidf, 1);
-                    const unsigned t2 = __shfl_up_sync(0xffffffffu, tidf, 2);
-                    const unsigned o1 = __shfl_up_sync(0xffffffffu, op, 1);
-                    const unsigned o2 = __shfl_up_sync(0xffffffffu, op, 2);
-                    const bool a1 = lane >= 1 && ((am >> (lane - 1)) & 1u);
-                    const bool a2 = lane >= 2 && ((am >> (lane - 2)) & 1u);
-                    // an exact repeat (same word, thread, op, wave) of an access a lower
-                    // lane applies adds nothing to the summary: drop it
-                    const bool dup = a && ((a1 && w1 == widx && t1 == tidf && o1 == op) ||
-                                           (a2 && w2 == widx && t2 == tidf && o2 == op));
-                    if (dup) {
-                        a = false;
-                        act[k] = false;
-                        c_merged++;
-                    }
-                    // other same-word lanes nearby: group them and let the lowest lane fold
-                    const bool near = a && ((a1 && w1 == widx) || (a2 && w2 == widx));
-                    if (__any_sync(0xffffffffu, near)) {
-                        my_acc[k * 32 + lane] = Acc{tidf, op};
-                        const unsigned am2 = __ballot_sync(0xffffffffu, a);
-                        const unsigned m = __match_any_sync(0xffffffffu, a ? widx : 0xFFFFFFFFu) & am2;
-                        if (a) {
+                    const unsigned mw = __match_any_sync(0xffffffffu, a ? widx : 0xFFFFFFFFu) & am;
+                    if (__any_sync(0xffffffffu, a && mw != (1u << lane))) {
+                        // an exact repeat (same word, thread, op, wave) of a lower lane's
+                        // access adds nothing to the summary: drop it
+                        const unsigned me =
+                            __match_any_sync(0xffffffffu, ((unsigned long long)tidf << 32) | op) & mw;
+                        if (a && (unsigned)(__ffs(me) - 1) != lane) {
+                            a = false;
+                            act[k] = false;
+                            c_merged++;
+                        }
+                        // distinct accesses to one word: the lowest lane folds them
+                        const unsigned m = mw & __ballot_sync(0xffffffffu, a);
+                        if (a && m != (1u << lane)) {
+                            my_acc[k * 32 + lane] = Acc{tidf, op};
                             grp[k] = m;
                             if ((unsigned)(__ffs(m) - 1) != lane) {
                                 act[k] = false;  // folded by the group leader
@@ -1094,10 +1156,23 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 }
             }
             bool need[HR_RPL];
+            unsigned long long fin[HR_RPL];  // the word's value after this access, when known
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
                 need[k] = act[k] && (spec || nv[k] != o[k]);
+                fin[k] = nv[k];
                 if (need[k]) nv[k] = hr_shadow_cas(shadow, word[k], o[k], nv[k], g);  // nv now holds the value seen
+            }
+            if (cache_on) {
+#pragma unroll
+                for (int k = 0; k < HR_RPL; ++k) {
+                    // a first CAS that stuck, or no change: fin is the word's value now
+                    if (!act[k] || (need[k] && nv[k] != o[k])) continue;
+                    const unsigned st = (unsigned)(fin[k] >> HR_SH_STATE_SHIFT);
+                    if (((s_absorb[0] | s_absorb[1] | s_absorb[2]) >> st) & 1u)
+                        st_relaxed_shared_u64(s_cache + (word[k] & (HR_WORD_CACHE - 1u)),
+                                              ((unsigned long long)((ctag << 5) | st) << 32) | word[k]);
+                }
             }
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
@@ -1106,6 +1181,22 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 bool done = nv[k] == o[k];
                 if (!done) {
                     c_retry++;
+                    // Most lost CASes lost to an equal transition (another lane of this
+                    // warp, or another CTA, applied the same access pattern first): the
+                    // value seen then already absorbs this access.  One inline look at
+                    // it settles that case without the out-of-line retry loop.
+                    if (grp[k] == (1u << lane)) {
+                        unsigned r2 = 0;
+                        const unsigned long long n2 =
+                            hr_fsm_step(nv[k], tidv[k], opv[k], bc, wc, ktag, g, s_table, &r2);
+                        if (n2 == nv[k]) {
+                            done = true;
+                            raced[k] = 0;  // no change: this access moved nothing into RACE
+                            who[k] = lane;
+                        }
+                    }
+                }
+                if (!done) {
                     const Retry r = retry_cas(shadow, word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc,
                                               wc, ktag, g, s_table, w.cas_cap);
                     c_cas += r.attempts;
@@ -1123,26 +1214,9 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                 }
             }
             }  // first-race mode
-            count(c_acc, c_cas, c_retry, c_merged);
+            count(c_acc + c_skip, c_cas, c_retry, c_merged + c_skip);
         }
-        // the warp's part of the tile is done; the CTA's last warp to finish it
-        // publishes one completion for the stage (counters indexed by tile number
-        // mod 2*ring never mix two tiles: a warp cannot finish tile it+2*ring
-        // before every warp has finished tile it)
-        __syncwarp();
-        if (lane == 0) {
-            const unsigned old = smem_add_acq_rel(&s_fin[it % (2 * HR_RING)], 1u);
-            if ((old + 1u) % HR_CONSUMERS == 0) {
-                hr_stage* st = &w.stages[t_stage & 0x7FFFFFFFu];
-                if (t_stage >> 31) {
-                    // the job's last stage: the tile that completes it stamps the job's end
-                    const unsigned prev = atom_add_release(&st->done, 1u);
-                    if (prev + 1u == st[1].item_begin - st->item_begin) w.jobs[st->job].done_ns = globaltimer();
-                } else {
-                    red_release_add(&st->done, 1u);
-                }
-            }
-        }
+        publish(it, t_stage);
     }
     flush();
 }

@@ -129,3 +129,97 @@ def test_table_multi_kernel_and_wide_blocks(oracle_mod, table):
         tr = tg.build_trace(kernels)
         keys = O.race_keys(O.bruteforce(tr, bd, ws))
         assert set(emulate(tr, table[0], bd, ws)) == keys
+
+
+def _absorbing(t, op):
+    """States that every (thread relation, sync relation) of `op` leads back to,
+    at grid level or RACE: the per-op set the per-wave checker's word cache uses."""
+    out = set()
+    for s in range(32):
+        es = [int(t[(s << 6) | (op << 4) | (trel << 2) | srel]) for trel in range(4) for srel in range(3)]
+        if all(e != 0xFF and (e & 31) == s and (e >> 5) >= 4 for e in es):
+            out.add(s)
+    return out
+
+
+def test_absorbing_states_stay_absorbing(table):
+    """A word cached in a state that absorbs op may be skipped for op for the
+    rest of a kernel only if no access by anyone can move it to a state that
+    does not: each op's absorbing set is closed under every transition."""
+    from paper_2401_04701_gb300 import hirace
+    t, _ = table
+    sets = [_absorbing(t, op) for op in range(3)]
+    names = [{hirace.state_name(s) for s in ss} for ss in sets]
+    assert names[0] == {"GREAD", "RACE"}
+    assert names[2] == {"GATOMIC", "RACE"}
+    assert names[1] == {"RACE"}                      # writes: only RACE absorbs them
+    for ss in sets:
+        for s in ss:
+            for op in range(3):
+                for trel in range(4):
+                    for srel in range(3):
+                        nxt = int(t[(s << 6) | (op << 4) | (trel << 2) | srel]) & 31
+                        assert nxt in ss, (hirace.state_name(s), op, trel, srel, hirace.state_name(nxt))
+
+
+def _step_pow2(t, o, tid, op, bc, wc, ktag, bd_shift, ws_shift):
+    """One transition of a packed shadow value, power-of-two geometry, the way
+    the device applies the table (kernel-tag check, compareTids, checkSync,
+    lookup, canonical packing)."""
+    ohi = o >> 32
+    os_ = ohi >> 27
+    if os_ != 0 and ((ohi >> 24) & 7) != ktag:
+        os_ = 0
+    x = tid ^ (o & 0xFFFFFFFF)
+    trel = 0 if x == 0 else (3 if x >> bd_shift else (2 if x >> ws_shift else 1))
+    obc, owc = (ohi >> 8) & 0xFFFF, ohi & 0xFF
+    srel = 2 if bc != obc else (1 if wc != owc else 0)
+    e = int(t[(os_ << 6) | (op << 4) | (trel << 2) | srel])
+    assert e != 0xFF
+    ns, lvl = e & 31, e >> 5
+    hi, lo = (ns << 27) | (ktag << 24), 0
+    if 1 <= lvl <= 3:
+        low = 0 if lvl == 1 else (min(ws_shift, bd_shift) if lvl == 2 else bd_shift)
+        lo = tid & ~((1 << low) - 1)
+        hi |= (bc << 8) | (0 if lvl == 3 else wc)
+    return (hi << 32) | lo
+
+
+def test_an_applied_access_stays_absorbed(table):
+    """Warp aggregation drops an access that repeats another lane's (same word,
+    thread, op, wave), whatever else reaches the word in between.  That needs
+    two facts of the table, checked here on every shadow value reachable in a
+    2-block x 2-warp x 2-thread grid over several clock pairs and two kernel
+    tags: re-applying an access is a no-op (step(step(S, a), a) ==
+    step(S, a)), and once a is absorbed it stays absorbed under any access b
+    of the same wave (step(S, a) == S implies step(step(S, b), a) ==
+    step(S, b))."""
+    t, _ = table
+    bd, ws = 2, 1
+    clocks = [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0)]
+    accs = [(tid, op) for tid in range(8) for op in range(3)]
+    seen, frontier = {0}, [0]
+    while frontier:
+        nxt = []
+        for s in frontier:
+            for ktag in (0, 1):
+                for bc, wc in clocks:
+                    for tid, op in accs:
+                        n = _step_pow2(t, s, tid, op, bc, wc, ktag, bd, ws)
+                        if n not in seen:
+                            seen.add(n)
+                            nxt.append(n)
+        frontier = nxt
+    assert len(seen) > 300
+    for s in seen:
+        for ktag in (0, 1):
+            for bc, wc in clocks:
+                st = {a: _step_pow2(t, s, *a, bc, wc, ktag, bd, ws) for a in accs}
+                for a in accs:
+                    sa = st[a]
+                    assert _step_pow2(t, sa, *a, bc, wc, ktag, bd, ws) == sa, (hex(s), a)
+                    if sa != s:
+                        continue
+                    for b in accs:
+                        sb = st[b]
+                        assert _step_pow2(t, sb, *a, bc, wc, ktag, bd, ws) == sb, (hex(s), a, b)
