@@ -270,10 +270,6 @@ constexpr unsigned hr_variant_tile(unsigned v)
 constexpr int HR_RING = HR_RING_DEPTH;                   // tiles in flight in shared memory
 constexpr unsigned HR_TICKET_BATCH = HR_BATCH;           // tiles a producer claims per ticket
 constexpr unsigned HR_CLEAR_WORDS = 1u << 16;  // shadow words per clear item
-#ifndef HR_WORD_CACHE_ENTRIES
-#define HR_WORD_CACHE_ENTRIES 2048
-#endif
-constexpr unsigned HR_WORD_CACHE = HR_WORD_CACHE_ENTRIES;  // per-CTA cache of words whose state absorbs an op
 constexpr unsigned HR_MAX_INTERVALS = 1u << 16;      // pre-pass intervals of a single-trace check
 constexpr unsigned HR_BATCH_INTERVALS = 1u << 18;    // pre-pass intervals of a batch
 constexpr unsigned long long HR_KEY_MASK = 0xFFFFFFFFFFFFull;

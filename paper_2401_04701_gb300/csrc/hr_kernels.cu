@@ -525,29 +525,18 @@ template <int RPL, int CONS>
 struct Shape {
     static constexpr int TILE = CONS * 32 * RPL;
     static constexpr int THREADS = (CONS + 1) * 32;
+    static constexpr int SLOTS = CONS * RPL * 32;  // records a tile gives its consumer lanes
     static constexpr size_t REC = (size_t)HR_RING * TILE * sizeof(uint4);
-    static constexpr size_t ACC = (size_t)CONS * RPL * 32 * sizeof(Acc);
-    // records, FSM table, aggregation scratch, tile infos, full/empty mbarriers,
-    // tile-finish counters, per-warp geometry and diagnostics
-    static constexpr size_t BYTES = REC + 2048 + ACC + HR_RING * sizeof(TileInfo) + 2 * HR_RING * 8 +
-                                    2 * HR_RING * 4 + CONS * sizeof(hr_geom) + CONS * 4 * 4 +
-                                    CONS * sizeof(hr_filter) + HR_WORD_CACHE * 8 + 16;
+    // records ring, FSM table, per-slot decoded access (tid, op), word and
+    // (group mask, race), tile infos, full/empty mbarriers, tile-finish
+    // counters, per-warp geometry and filter
+    static constexpr size_t BYTES = REC + 2048 + (size_t)SLOTS * (sizeof(Acc) + 4 + 8) + HR_RING * sizeof(TileInfo) +
+                                    2 * HR_RING * 8 + 2 * HR_RING * 4 + CONS * sizeof(hr_geom) +
+                                    CONS * sizeof(hr_filter);
     static constexpr int MIN_CTAS = CONS >= 8 ? HR_MIN_CTAS : 4;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long ld_relaxed_shared_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.cta.shared.u64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)));
-    return v;
-}
-
-__device__ __forceinline__ void st_relaxed_shared_u64(unsigned long long* p, unsigned long long v)
-{
-    asm volatile("st.relaxed.cta.shared.u64 [%0], %1;" ::"r"(smem_u32(p)), "l"(v));
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
@@ -746,6 +735,11 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
     bool have = false, skip = false;
     unsigned pend = 0, pend_end = 0, polls = 0;
     unsigned known = HR_NO_DEP;  // last dependency seen complete
+    // Tickets are claimed one batch ahead, so the claim's round trip to L2
+    // overlaps the wait for a free slot instead of delaying every tile.  A
+    // claimed tile only waits on stages of lower tickets, so holding one
+    // blocks nobody.
+    unsigned next = atomicAdd(&w.ctl->ticket, HR_TICKET_BATCH);
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (it >= HR_RING &&
@@ -754,9 +748,10 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
             mbar_arrive(&s_full[b]);
             return;
         }
-        if (pend == pend_end) {  // claim the next batch of tiles
-            pend = atomicAdd(&w.ctl->ticket, HR_TICKET_BATCH);
+        if (pend == pend_end) {  // take the batch claimed ahead, claim the one after it
+            pend = next;
             pend_end = min(pend + HR_TICKET_BATCH, total);
+            if (pend < total) next = atomicAdd(&w.ctl->ticket, HR_TICKET_BATCH);
             ++polls;
         }
         const unsigned t = pend++;
@@ -819,55 +814,27 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
 
 template <bool AGG, int HR_RPL, int HR_CONSUMERS, bool EVERY>
 __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR_RPL, HR_CONSUMERS>::MIN_CTAS)
-    hr_check_kernel(hr_region_dev* __restrict__ regions,
-                                                                 hr_work w,
-                                                                 const unsigned char* __restrict__ gtable)
+    hr_check_kernel(hr_region_dev* __restrict__ regions, hr_work w, const unsigned char* __restrict__ gtable)
 {
     using S = Shape<HR_RPL, HR_CONSUMERS>;
     constexpr int HR_TILE = S::TILE;
     constexpr int HR_THREADS = S::THREADS;
-    constexpr size_t SMEM_REC = S::REC;
-    constexpr size_t SMEM_ACC = S::ACC;
     extern __shared__ __align__(128) unsigned char smem[];
-    uint4* s_rec = reinterpret_cast<uint4*>(smem);
-    unsigned char* s_table = smem + SMEM_REC;
-    Acc* s_acc = reinterpret_cast<Acc*>(s_table + 2048);
-    TileInfo* s_info = reinterpret_cast<TileInfo*>(smem + SMEM_REC + 2048 + SMEM_ACC);
+    uint4* s_rec = reinterpret_cast<uint4*>(smem);                                  // [HR_RING][HR_TILE]
+    unsigned char* s_table = smem + S::REC;                                         // [2048]
+    Acc* s_acc = reinterpret_cast<Acc*>(s_table + 2048);                            // [SLOTS]: (tid, op)
+    unsigned* s_word = reinterpret_cast<unsigned*>(s_acc + S::SLOTS);               // [SLOTS]: shadow index
+    uint2* s_aux = reinterpret_cast<uint2*>(s_word + S::SLOTS);                     // [SLOTS]: (group, race)
+    TileInfo* s_info = reinterpret_cast<TileInfo*>(s_aux + S::SLOTS);               // [HR_RING]
     uint64_t* s_full = reinterpret_cast<uint64_t*>(s_info + HR_RING);
     uint64_t* s_empty = s_full + HR_RING;
-    unsigned* s_fin = reinterpret_cast<unsigned*>(s_empty + HR_RING);  // [2 * HR_RING]
-    hr_geom* s_geom = reinterpret_cast<hr_geom*>(s_fin + 2 * HR_RING);  // [HR_CONSUMERS]
-    unsigned* s_cnt = reinterpret_cast<unsigned*>(s_geom + HR_CONSUMERS);  // [HR_CONSUMERS][4]
-    hr_filter* s_filt = reinterpret_cast<hr_filter*>(s_cnt + 4 * HR_CONSUMERS);  // [HR_CONSUMERS]
-    // Words whose state absorbs an op for the rest of a kernel, seen by this CTA:
-    // ((region, kernel) tag << 5 | state) << 32 | word, direct-mapped by word.
-    // A grid-level state (GREAD, GATOMIC) stays itself or becomes RACE, and RACE
-    // stays RACE, so an access whose op the cached state absorbs changes
-    // nothing, whatever other CTAs did to the word since: it is applied without
-    // touching the shadow.  Entries are read and written whole (relaxed 64-bit
-    // accesses), so a reader never pairs one word with another's state.
-    unsigned long long* s_cache = reinterpret_cast<unsigned long long*>(s_filt + HR_CONSUMERS);  // [HR_WORD_CACHE]
-    unsigned* s_absorb = reinterpret_cast<unsigned*>(s_cache + HR_WORD_CACHE);  // [3]: states absorbing op
+    unsigned* s_fin = reinterpret_cast<unsigned*>(s_empty + HR_RING);               // [2 * HR_RING]
+    hr_geom* s_geom = reinterpret_cast<hr_geom*>(s_fin + 2 * HR_RING);              // [HR_CONSUMERS]
+    hr_filter* s_filt = reinterpret_cast<hr_filter*>(s_geom + HR_CONSUMERS);        // [HR_CONSUMERS]
 
     const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (unsigned i = threadIdx.x; i < 256; i += HR_THREADS)
         reinterpret_cast<uint2*>(s_table)[i] = reinterpret_cast<const uint2*>(gtable)[i];
-    for (unsigned i = threadIdx.x; i < HR_WORD_CACHE; i += HR_THREADS) s_cache[i] = ~0ull;
-    if (threadIdx.x < 3) {
-        // a state absorbs op when every (thread relation, sync relation) of op
-        // leads back to it; only grid-level states and RACE are kept
-        const unsigned op = threadIdx.x;
-        unsigned m = 0;
-        for (unsigned st = 0; st < 32; ++st) {
-            bool all = true;
-            for (unsigned r = 0; r < 12 && all; ++r) {
-                const unsigned e = __ldg(gtable + ((st << 6) | (op << 4) | ((r / 3) << 2) | (r % 3)));
-                all = e != 0xFFu && (e & 31u) == st && (e >> 5) >= HR_LVL_GRID;
-            }
-            if (all) m |= 1u << st;
-        }
-        s_absorb[threadIdx.x] = m;
-    }
     if (threadIdx.x == 0) {
         for (int b = 0; b < HR_RING; ++b) {
             mbar_init(&s_full[b], 1);
@@ -892,34 +859,22 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
     bool filtering = false;  // the region's filter selects only part of the accesses
     unsigned long long* shadow = nullptr;
     unsigned long long n_words = 0;
+    unsigned tid_hi = 0;     // tid bits the region's shadow packing cannot hold
+    // this warp's slots: lane + 32 k holds the lane's k-th record of the tile
     Acc* my_acc = s_acc + (size_t)wid * HR_RPL * 32;
+    unsigned* my_word = s_word + (size_t)wid * HR_RPL * 32;
+    uint2* my_aux = s_aux + (size_t)wid * HR_RPL * 32;
     unsigned known = HR_NO_DEP;  // last dependency this warp has seen complete
-    // diagnostics: lane counts summed per tile into this warp's shared counters
-    unsigned* cnt = s_cnt + wid * 4;
-    if (lane < 4) cnt[lane] = 0;
-    __syncwarp();
-    auto count = [&](unsigned acc_n, unsigned cas_n, unsigned retry_n, unsigned merged_n) {
-        unsigned v[4] = {acc_n, cas_n, retry_n, merged_n};
+    // diagnostics: this lane's counts since the warp last added them to the region
+    unsigned lc_acc = 0, lc_cas = 0, lc_retry = 0, lc_merged = 0;
+    auto flush = [&]() {
+        unsigned long long v[4] = {lc_acc, lc_cas, lc_retry, lc_merged};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            unsigned x = v[i];
-            if (__any_sync(0xffffffffu, x != 0)) {
-                for (int o2 = 16; o2 > 0; o2 >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o2);
-                if (lane == 0) cnt[i] += x;
-            }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o2);
+            if (lane == 0 && region && v[i]) atomicAdd(&region->counters[i], v[i]);
         }
-    };
-    auto flush = [&]() {
-        __syncwarp();
-        if (lane == 0 && region) {
-            if (cnt[0]) atomicAdd(&region->counters[0], (unsigned long long)cnt[0]);
-            if (cnt[1]) atomicAdd(&region->counters[1], (unsigned long long)cnt[1]);
-            if (cnt[2]) atomicAdd(&region->counters[2], (unsigned long long)cnt[2]);
-            if (cnt[3]) atomicAdd(&region->counters[3], (unsigned long long)cnt[3]);
-        }
-        __syncwarp();
-        if (lane < 4) cnt[lane] = 0;
-        __syncwarp();
+        lc_acc = lc_cas = lc_retry = lc_merged = 0;
     };
     // The warp's part of tile `tn` (stage `stage`, bit 31: the job's last) is
     // done: the CTA's last warp to finish the tile publishes one completion for
@@ -942,12 +897,21 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             }
         }
     };
+    // Bounded wait for the tile's dependency; false when the check is aborting.
+    auto wait_dep = [&](unsigned dep, unsigned need) {
+        bool ok = true;
+        if (lane == 0) ok = stage_wait(&w.stages[dep].done, need, &w.ctl->abort, &region->error, w.wait_ns);
+        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+        __syncwarp();
+        if (ok) known = dep;
+        return ok;
+    };
+
     for (unsigned it = 0;; ++it) {
         const unsigned b = it % HR_RING;
         if (!mbar_wait(&s_full[b], (it / HR_RING) & 1u, &w.ctl->abort, region ? &region->error : &regions[0].error,
                        w.wait_ns))
             break;
-        // take what the tile needs out of the slot, then release it
         const TileInfo& ti = s_info[b];
         if (!ti.valid) break;
         const unsigned t_type = ti.type, t_skip = ti.skip, t_dep = ti.dep;
@@ -958,15 +922,10 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         const unsigned bcwc = (unsigned)ti.key;
         const unsigned kb = (unsigned)(ti.kb >> 32);     // the job's kernel base
         const bool records = t_type == HR_STAGE_RECORDS && !t_skip;
-        uint4 rec[HR_RPL];
-        const unsigned base = wid * 32 * HR_RPL + lane;
-#pragma unroll
-        for (int k = 0; k < HR_RPL; ++k) {
-            const unsigned idx = base + k * 32;
-            rec[k] = (records && idx < t_n) ? s_rec[(size_t)b * HR_TILE + idx] : make_uint4(0, 0, 0, 0xFFFFFFFFu);
+        if (!records) {  // nothing to read from the slot
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[b]);
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[b]);  // the slot may be refilled now
         if (t_region != cur) {
             flush();
             cur = t_region;
@@ -979,6 +938,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             filtering = hr_filter_active(filt);
             shadow = region->shadow;
             n_words = region->n_words;
+            tid_hi = (g.shadow_bytes == 4 && g.tid_bits < 32) ? ~((1u << g.tid_bits) - 1u) : 0u;
         }
 
         bool ready = t_dep == HR_NO_DEP || t_dep == known || t_ready;
@@ -991,14 +951,7 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
         if (ready && t_dep != HR_NO_DEP) known = t_dep;
 
         if (t_type == HR_STAGE_CLEAR && !t_skip) {
-            if (!ready) {
-                bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
-                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                __syncwarp();
-                if (!ok) break;
-                known = t_dep;
-            }
+            if (!ready && !wait_dep(t_dep, t_need)) break;
             // bytes [bb, be) of the shadow: 16-byte stores, a 4-byte tail
             const unsigned long long sb = g.shadow_bytes;
             const unsigned long long span = (unsigned long long)(HR_CLEAR_WORDS / HR_CONSUMERS) * sb;
@@ -1015,23 +968,30 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
             const unsigned bc = bcwc >> 16;
             const unsigned wc = bcwc & 0xFFFFu;
             const unsigned ktag = kern & 7u;
-            // the word cache's tag of this tile's (region, kernel); off when it does not fit 27 bits
-            const bool cache_on = !EVERY && t_region < 1024u && kern < (1u << 17) &&
-                                  g.report_mode != HR_REPORT_EVERY_EPOCH;
-            const unsigned ctag = (t_region << 17) | kern;
-            unsigned c_skip = 0;
             // non-absorbing reports: only the EVERY instantiation carries that path
             const bool every = EVERY && g.report_mode == HR_REPORT_EVERY_EPOCH;
+            // the wave's clocks fit the region's shadow packing (else every access overflows it)
+            const bool clk_fit = g.shadow_bytes != 4 ? (bc <= HR_BC_MAX && wc <= HR_WC_MAX)
+                                                     : ((wc >> hr_wc_bits(g)) == 0 && (bc >> hr_bc_bits(g)) == 0);
+            // Phase 1: decode the lane's records, drop or group repeats (warp
+            // aggregation), note each access in the warp's slots and issue every
+            // shadow load of the tile at once.  When the previous stage is still
+            // running the loads go out before waiting for it (they overlap the
+            // wait) and may be stale: every CAS then goes out, so a stale value
+            // fails and is refolded from the value the CAS returns.
+            const uint4* trec = s_rec + (size_t)b * HR_TILE;
+            const unsigned base = wid * 32 * HR_RPL + lane;
             unsigned err = 0;
-            unsigned c_acc = 0, c_cas = 0, c_retry = 0, c_merged = 0;
-            unsigned word[HR_RPL], grp[HR_RPL], tidv[HR_RPL], opv[HR_RPL];
-            bool act[HR_RPL];
+            unsigned actm = 0;  // bit k: slot k applies an access (a group's leader applies the group)
+            unsigned grpm = 0;  // bit k: slot k leads a group of distinct accesses to one word
+            unsigned long long o[HR_RPL];
 #pragma unroll
             for (int k = 0; k < HR_RPL; ++k) {
-                const uint4 v = rec[k];
+                const unsigned idx = base + k * 32;
+                const bool in = idx < t_n;
+                const uint4 v = in ? trec[idx] : make_uint4(0, 0, 0, 0xFFFFFFFFu);
                 const unsigned op = (v.w >> 16) & 0xFFu;
                 const unsigned flags = v.w >> 24;
-                const bool in = base + k * 32 < t_n;
                 // record key (kernel + kernel base, bc, wc) against the wave's
                 const bool same_wave = v.z == bcwc && (v.w & 0xFFFFu) + kb == kern;
                 bool a = in && op <= HR_A;
@@ -1053,25 +1013,13 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                         err = HR_ERR_RANGE;
                 }
                 a = a && same_wave && mon && widx < n_words;
-                if (a && !hr_fits(tidf, bc, wc, g)) {
+                if (a && (!clk_fit || (tidf & tid_hi))) {
                     err = HR_ERR_CLOCK_OVERFLOW;  // tid, bc or wc wider than the shadow packing
                     a = false;
                 }
-                if (cache_on && a) {  // a cached state that absorbs this op: nothing to do
-                    const unsigned long long ce = ld_relaxed_shared_u64(s_cache + (widx & (HR_WORD_CACHE - 1u)));
-                    const unsigned cy = (unsigned)(ce >> 32);
-                    if ((unsigned)ce == widx && (cy >> 5) == ctag && ((s_absorb[op] >> (cy & 31u)) & 1u)) {
-                        a = false;
-                        c_skip++;
-                    }
-                }
-                act[k] = a;
-                word[k] = widx;
-                tidv[k] = tidf;
-                opv[k] = op;
-                grp[k] = 1u << lane;
+                lc_acc += a;
                 if (AGG && !every) {
-                    // lanes of this unit applying the same word
+                    // lanes of this slot applying the same word
                     const unsigned am = __ballot_sync(0xffffffffu, a);
                     const unsigned mw = __match_any_sync(0xffffffffu, a ? widx : 0xFFFFFFFFu) & am;
                     if (__any_sync(0xffffffffu, a && mw != (1u << lane))) {
@@ -1081,140 +1029,119 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
                             __match_any_sync(0xffffffffu, ((unsigned long long)tidf << 32) | op) & mw;
                         if (a && (unsigned)(__ffs(me) - 1) != lane) {
                             a = false;
-                            act[k] = false;
-                            c_merged++;
+                            lc_merged++;
                         }
                         // distinct accesses to one word: the lowest lane folds them
                         const unsigned m = mw & __ballot_sync(0xffffffffu, a);
                         if (a && m != (1u << lane)) {
-                            my_acc[k * 32 + lane] = Acc{tidf, op};
-                            grp[k] = m;
                             if ((unsigned)(__ffs(m) - 1) != lane) {
-                                act[k] = false;  // folded by the group leader
-                                c_merged++;
+                                a = false;  // folded by the group leader
+                                lc_merged++;
+                            } else {
+                                grpm |= 1u << k;
+                                my_aux[k * 32 + lane].x = m;
                             }
                         }
                     }
                 }
+                my_acc[k * 32 + lane] = Acc{tidf, op};
+                my_word[k * 32 + lane] = widx;
+                if (a && !every) o[k] = hr_shadow_load(shadow, widx, g);
+                actm |= (unsigned)a << k;
             }
-            if (err) hr_set_error(&region->error, err);
             __syncwarp();
+            if (lane == 0) mbar_arrive(&s_empty[b]);  // decoded: the slot may be refilled
+            if (err) hr_set_error(&region->error, err);
 
             if (every) {
-                if (!ready) {
-                    bool ok = true;
-                    if (lane == 0)
-                        ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
-                    ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                    __syncwarp();
-                    if (!ok) break;
-                    known = t_dep;
-                }
+                if (!ready && !wait_dep(t_dep, t_need)) break;
 #pragma unroll
                 for (int k = 0; k < HR_RPL; ++k) {
-                    if (!act[k]) continue;
-                    c_acc++;
-                    const unsigned abs_word = word[k] + (filtering ? (unsigned)filt.word_lo : 0u);
-                    const unsigned st = every_epoch_record(shadow, n_words, word[k], abs_word, tidv[k], opv[k], bc,
-                                                           wc, kern, g, region, w.cas_cap);
+                    if (!((actm >> k) & 1u)) continue;
+                    const Acc me = my_acc[k * 32 + lane];
+                    const unsigned wd = my_word[k * 32 + lane];
+                    const unsigned abs_word = wd + (filtering ? (unsigned)filt.word_lo : 0u);
+                    const unsigned st = every_epoch_record(shadow, n_words, wd, abs_word, me.tid, me.op, bc, wc,
+                                                           kern, g, region, w.cas_cap);
                     if (st) hr_set_error(&region->error, st);
                 }
             } else {
-            // Shadow values.  When the previous stage is still running they are
-            // loaded before waiting for it (the loads overlap the wait) and may be
-            // stale: every CAS then goes out, so a stale value fails and is refolded
-            // from the value the CAS returns.
-            unsigned long long o[HR_RPL], nv[HR_RPL];
-#pragma unroll
-            for (int k = 0; k < HR_RPL; ++k)
-                if (act[k]) o[k] = hr_shadow_load(shadow, word[k], g);
-            const bool spec = !ready;
-            if (!ready) {
-                bool ok = true;
-                if (lane == 0) ok = stage_wait(&w.stages[t_dep].done, t_need, &w.ctl->abort, &region->error, w.wait_ns);
-                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-                __syncwarp();
-                if (!ok) break;
-                known = t_dep;
-            }
-            unsigned raced[HR_RPL], who[HR_RPL];
-#pragma unroll
-            for (int k = 0; k < HR_RPL; ++k) {
-                raced[k] = 0;
-                who[k] = lane;
-                if (act[k]) {
-                    if (grp[k] == (1u << lane)) {
-                        c_acc++;
-                        nv[k] = hr_fsm_step(o[k], tidv[k], opv[k], bc, wc, ktag, g, s_table, &raced[k]);
-                    } else {
-                        c_acc += __popc(grp[k]);
-                        const Fold f = fold_group(o[k], grp[k], my_acc + k * 32, bc, wc, ktag, g, s_table);
-                        nv[k] = f.n;
-                        raced[k] = f.raced;
-                        who[k] = f.who;
-                    }
-                }
-            }
-            bool need[HR_RPL];
-            unsigned long long fin[HR_RPL];  // the word's value after this access, when known
-#pragma unroll
-            for (int k = 0; k < HR_RPL; ++k) {
-                need[k] = act[k] && (spec || nv[k] != o[k]);
-                fin[k] = nv[k];
-                if (need[k]) nv[k] = hr_shadow_cas(shadow, word[k], o[k], nv[k], g);  // nv now holds the value seen
-            }
-            if (cache_on) {
+                const bool spec = !ready;
+                if (!ready && !wait_dep(t_dep, t_need)) break;
+                // Phase 2: fold each access into its loaded value and send out every
+                // CAS of the tile before reading any of their results.
+                unsigned long long seen[HR_RPL];
+                unsigned casm = 0;  // bit k: a CAS went out for slot k
+                unsigned racem = 0; // bit k: slot k's fold moves the word into RACE (details in my_aux.y)
 #pragma unroll
                 for (int k = 0; k < HR_RPL; ++k) {
-                    // a first CAS that stuck, or no change: fin is the word's value now
-                    if (!act[k] || (need[k] && nv[k] != o[k])) continue;
-                    const unsigned st = (unsigned)(fin[k] >> HR_SH_STATE_SHIFT);
-                    if (((s_absorb[0] | s_absorb[1] | s_absorb[2]) >> st) & 1u)
-                        st_relaxed_shared_u64(s_cache + (word[k] & (HR_WORD_CACHE - 1u)),
-                                              ((unsigned long long)((ctag << 5) | st) << 32) | word[k]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < HR_RPL; ++k) {
-                if (!need[k]) continue;
-                c_cas++;
-                bool done = nv[k] == o[k];
-                if (!done) {
-                    c_retry++;
-                    // Most lost CASes lost to an equal transition (another lane of this
-                    // warp, or another CTA, applied the same access pattern first): the
-                    // value seen then already absorbs this access.  One inline look at
-                    // it settles that case without the out-of-line retry loop.
-                    if (grp[k] == (1u << lane)) {
-                        unsigned r2 = 0;
-                        const unsigned long long n2 =
-                            hr_fsm_step(nv[k], tidv[k], opv[k], bc, wc, ktag, g, s_table, &r2);
-                        if (n2 == nv[k]) {
-                            done = true;
-                            raced[k] = 0;  // no change: this access moved nothing into RACE
-                            who[k] = lane;
+                    if (!((actm >> k) & 1u)) continue;
+                    unsigned r = 0, who = lane;
+                    unsigned long long nv;
+                    if (AGG && ((grpm >> k) & 1u)) {
+                        const Fold f = fold_group(o[k], my_aux[k * 32 + lane].x, my_acc + k * 32, bc, wc, ktag, g,
+                                                  s_table);
+                        nv = f.n;
+                        r = f.raced;
+                        who = f.who;
+                    } else {
+                        const Acc me = my_acc[k * 32 + lane];
+                        nv = hr_fsm_step(o[k], me.tid, me.op, bc, wc, ktag, g, s_table, &r);
+                    }
+                    if (spec || nv != o[k]) {
+                        seen[k] = hr_shadow_cas(shadow, my_word[k * 32 + lane], o[k], nv, g);
+                        casm |= 1u << k;
+                        if (r) {
+                            racem |= 1u << k;
+                            my_aux[k * 32 + lane].y = r | (who << 8);
                         }
                     }
                 }
-                if (!done) {
-                    const Retry r = retry_cas(shadow, word[k], nv[k], tidv[k], opv[k], grp[k], my_acc + k * 32, bc,
-                                              wc, ktag, g, s_table, w.cas_cap);
-                    c_cas += r.attempts;
-                    raced[k] = r.raced;
-                    who[k] = r.who;
-                    done = r.ok != 0;
-                    if (!done) hr_set_error(&region->error, HR_ERR_CONTENTION);
+                // Phase 3: a CAS that returned the value it expected stuck.  One that
+                // lost mostly lost to an equal transition (another lane or CTA applied
+                // the same access pattern first): the value seen then already absorbs
+                // this access, which one inline look settles; otherwise refold and retry.
+#pragma unroll
+                for (int k = 0; k < HR_RPL; ++k) {
+                    if (!((casm >> k) & 1u)) continue;
+                    lc_cas++;
+                    unsigned raced = 0, who = lane;
+                    if ((racem >> k) & 1u) {
+                        const unsigned y = my_aux[k * 32 + lane].y;
+                        raced = y & 0xFFu;
+                        who = y >> 8;
+                    }
+                    bool done = seen[k] == o[k];
+                    if (!done) {
+                        lc_retry++;
+                        const Acc me = my_acc[k * 32 + lane];
+                        const unsigned m = (AGG && ((grpm >> k) & 1u)) ? my_aux[k * 32 + lane].x : (1u << lane);
+                        if (m == (1u << lane)) {
+                            unsigned r2 = 0;
+                            if (hr_fsm_step(seen[k], me.tid, me.op, bc, wc, ktag, g, s_table, &r2) == seen[k]) {
+                                done = true;
+                                raced = 0;  // no change: this access moved nothing into RACE
+                                who = lane;
+                            }
+                        }
+                        if (!done) {
+                            const Retry rr = retry_cas(shadow, my_word[k * 32 + lane], seen[k], me.tid, me.op, m,
+                                                       my_acc + k * 32, bc, wc, ktag, g, s_table, w.cas_cap);
+                            lc_cas += rr.attempts;
+                            raced = rr.raced;
+                            who = rr.who;
+                            done = rr.ok != 0;
+                            if (!done) hr_set_error(&region->error, HR_ERR_CONTENTION);
+                        }
+                    }
+                    if (done && raced) {
+                        const Acc ra = my_acc[k * 32 + who];
+                        const unsigned abs_word = my_word[k * 32 + lane] + (filtering ? (unsigned)filt.word_lo : 0u);
+                        hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, abs_word,
+                                       ra.tid, kern, bc, region->region, ra.op, raced - 1u);
+                    }
                 }
-                if (done && raced[k]) {
-                    const unsigned rt = who[k] == lane ? tidv[k] : my_acc[k * 32 + who[k]].tid;
-                    const unsigned ro = who[k] == lane ? opv[k] : my_acc[k * 32 + who[k]].op;
-                    const unsigned abs_word = word[k] + (filtering ? (unsigned)filt.word_lo : 0u);
-                    hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, abs_word, rt,
-                                   kern, bc, region->region, ro, raced[k] - 1u);
-                }
-            }
             }  // first-race mode
-            count(c_acc + c_skip, c_cas, c_retry, c_merged + c_skip);
         }
         publish(it, t_stage);
     }
