@@ -131,37 +131,6 @@ def test_table_multi_kernel_and_wide_blocks(oracle_mod, table):
         assert set(emulate(tr, table[0], bd, ws)) == keys
 
 
-def _absorbing(t, op):
-    """States that every (thread relation, sync relation) of `op` leads back to,
-    at grid level or RACE: the per-op set the per-wave checker's word cache uses."""
-    out = set()
-    for s in range(32):
-        es = [int(t[(s << 6) | (op << 4) | (trel << 2) | srel]) for trel in range(4) for srel in range(3)]
-        if all(e != 0xFF and (e & 31) == s and (e >> 5) >= 4 for e in es):
-            out.add(s)
-    return out
-
-
-def test_absorbing_states_stay_absorbing(table):
-    """A word cached in a state that absorbs op may be skipped for op for the
-    rest of a kernel only if no access by anyone can move it to a state that
-    does not: each op's absorbing set is closed under every transition."""
-    from paper_2401_04701_gb300 import hirace
-    t, _ = table
-    sets = [_absorbing(t, op) for op in range(3)]
-    names = [{hirace.state_name(s) for s in ss} for ss in sets]
-    assert names[0] == {"GREAD", "RACE"}
-    assert names[2] == {"GATOMIC", "RACE"}
-    assert names[1] == {"RACE"}                      # writes: only RACE absorbs them
-    for ss in sets:
-        for s in ss:
-            for op in range(3):
-                for trel in range(4):
-                    for srel in range(3):
-                        nxt = int(t[(s << 6) | (op << 4) | (trel << 2) | srel]) & 31
-                        assert nxt in ss, (hirace.state_name(s), op, trel, srel, hirace.state_name(nxt))
-
-
 def _step_pow2(t, o, tid, op, bc, wc, ktag, bd_shift, ws_shift):
     """One transition of a packed shadow value, power-of-two geometry, the way
     the device applies the table (kernel-tag check, compareTids, checkSync,
