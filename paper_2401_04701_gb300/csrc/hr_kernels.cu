@@ -610,15 +610,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsign
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*(volatile unsigned*)abort_flag) return false;
-        if (globaltimer() - t0 > wait_ns) {
-            atomicExch(abort_flag, 1u);
-            hr_set_error(err, HR_ERR_TIMEOUT);
-            return false;
+    for (unsigned n = 0;; ++n) {
+        if (mbar_try_wait(bar, parity)) return true;
+        // The abort flag and the clock are looked at every 32 tries only: reading
+        // the flag is a round trip to L2, and a phase that completes meanwhile
+        // would be noticed only after it.  Each try is itself bounded, so the
+        // wait stays bounded.
+        if ((n & 31u) == 31u) {
+            if (*(volatile unsigned*)abort_flag) return false;
+            if (globaltimer() - t0 > wait_ns) {
+                atomicExch(abort_flag, 1u);
+                hr_set_error(err, HR_ERR_TIMEOUT);
+                return false;
+            }
         }
     }
-    return true;
 }
 
 // Bounded wait until a stage's completion count reaches `need`.
