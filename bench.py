@@ -609,6 +609,17 @@ def run_gpu(args, rank, world, local_rank):
             raise SystemExit("end-to-end check failed: status %s, %d races" % (hirace.STATUS[status], n_total))
     e2e_s = time.perf_counter() - t0
     e2e_rate = world * n_acc * e2e_steps / e2e_s if e2e_steps else None
+    # the host link's own ceiling beside it: plain pinned H2D copies of the same bytes
+    h2d_gbs = None
+    if e2e_steps:
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        d_trace.copy_(host, non_blocking=True)
+        c0.record()
+        for _ in range(3):
+            d_trace.copy_(host, non_blocking=True)
+        c1.record()
+        torch.cuda.synchronize()
+        h2d_gbs = 3 * host.numel() / (c0.elapsed_time(c1) / 1e3) / 1e9
     latency = check_latency(ck, d_trace, stream, expect, args.latency_checks) if default else None
 
     if rank != 0:
@@ -656,7 +667,9 @@ def run_gpu(args, rank, world, local_rank):
                      "peak_kind": peak_kind, "alg_bytes_per_launch": alg_bytes,
                      "kernel_ms": check_ms, "prepass_ms": prof["prepass_ms"] / max(1, prof["calls"])},
         "e2e": {"value": e2e_rate, "unit": UNIT, "h2d_bytes_per_step": int(host.numel()),
-                "d2h_bytes_per_step": int(d2h // max(1, e2e_steps))},
+                "d2h_bytes_per_step": int(d2h // max(1, e2e_steps)),
+                "h2d_gbs_in_checks": host.numel() * e2e_steps / e2e_s / 1e9 if e2e_steps else None,
+                "pinned_h2d_copy_gbs": h2d_gbs},
         "fsm_counters": {k: int(v) for k, v in counters.items()},
         "gpu_launches": int(prof["launches"]),
         "autotune": {"chosen": best, "variant": dict(hirace.variants())[best],
