@@ -347,8 +347,8 @@ hr_status hr_destroy(hr_ctx* ctx);
  * and the odd id after each is the same shape without aggregation.  Id 6 is the
  * binned checker, which hr_variant_desc reports with zero records per lane and
  * zero consumer warps: the accesses are moved into (4096-word shadow segment,
- * wave) buckets and one CTA per segment applies them to a shared-memory copy of
- * the segment, wave by wave.  It takes single-trace checks of regions of at
+ * wave) buckets and persistent thread groups apply each segment's buckets to a
+ * shared-memory copy of the segment, wave by wave.  It takes single-trace checks of regions of at
  * most 2^26 words with at most 256 waves per call; batches, and calls it cannot
  * take, run the per-wave checker of id 3.  Its first check on a region
  * allocates the region's bucket tables (4 bytes per segment for each of 256

@@ -234,7 +234,7 @@ struct hr_variant {
     int rpl;         // records per consumer lane per tile
     int consumers;   // consumer warps per CTA (plus one producer warp)
 };
-constexpr hr_variant HR_VARIANTS[] = {{1, 4, 8}, {0, 4, 8}, {1, 2, 8}, {0, 2, 8}, {1, 8, 4}, {0, 8, 4}};
+constexpr hr_variant HR_VARIANTS[] = {{1, 4, 8}, {0, 4, 8}, {1, 2, 8}, {0, 2, 8}, {1, 1, 8}, {0, 1, 8}};
 constexpr unsigned HR_N_SHAPES = sizeof(HR_VARIANTS) / sizeof(HR_VARIANTS[0]);
 // The binned checker (hr_binned.cu): single-trace checks of first-race regions
 // only; batches, and checks it cannot take, run the per-wave checker of shape 3.

@@ -1219,8 +1219,8 @@ int hr_check_grid_size(unsigned variant)
     case 1: cached = grid_for<false, 4, 8>(); break;
     case 2: cached = grid_for<true, 2, 8>(); break;
     case 3: cached = grid_for<false, 2, 8>(); break;
-    case 4: cached = grid_for<true, 8, 4>(); break;
-    case 5: cached = grid_for<false, 8, 4>(); break;
+    case 4: cached = grid_for<true, 1, 8>(); break;
+    case 5: cached = grid_for<false, 1, 8>(); break;
     default: cached = grid_for<false, 2, 8, true>(); break;
     }
     return cached;
@@ -1289,8 +1289,8 @@ cudaError_t hr_launch_jobs(hr_region_dev* d_regions, const hr_work& w_in, const 
     case 1: launch_variant<false, 4, 8>(grid, d_regions, w, d_table, stream); break;
     case 2: launch_variant<true, 2, 8>(grid, d_regions, w, d_table, stream); break;
     case 3: launch_variant<false, 2, 8>(grid, d_regions, w, d_table, stream); break;
-    case 4: launch_variant<true, 8, 4>(grid, d_regions, w, d_table, stream); break;
-    case 5: launch_variant<false, 8, 4>(grid, d_regions, w, d_table, stream); break;
+    case 4: launch_variant<true, 1, 8>(grid, d_regions, w, d_table, stream); break;
+    case 5: launch_variant<false, 1, 8>(grid, d_regions, w, d_table, stream); break;
     default: launch_variant<false, 2, 8, true>(grid, d_regions, w, d_table, stream); break;
     }
     return cudaGetLastError();
