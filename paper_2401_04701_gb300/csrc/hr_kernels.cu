@@ -718,15 +718,100 @@ __device__ __forceinline__ Retry retry_cas(unsigned long long* shadow, unsigned 
     return r;
 }
 
-// Every-epoch mode: one access through the per-conflict-bit summaries (cold
-// relative to the first-race path, kept out of line).
-__device__ __noinline__ unsigned every_epoch_record(unsigned long long* shadow, unsigned long long n_words,
-                                                   unsigned idx, unsigned abs_word, unsigned tid, unsigned op,
-                                                   unsigned bc, unsigned wc, unsigned kern, const hr_geom& g,
-                                                   hr_region_dev* region, unsigned cap)
+// Every-epoch mode for a lane's RPL accesses at once (bit k of `act`: slot k
+// holds one): the steps of hr_ep_apply, each over every slot before the next,
+// so each step costs one round trip for all of them and one fence serves them
+// all.  Per access: fold it into the summaries of the conflict kinds it holds
+// (CAS loops), then a sequentially consistent fence, then read the summaries
+// of the kinds it conflicts with; a conflicting holder is reported once per
+// (word, kernel, epoch) through a CAS on the stamp word.  Of two concurrent
+// conflicting accesses at least one therefore sees the other.  Returns 0 or
+// HR_ERR_CONTENTION when a CAS loop reached `cap` tries.
+template <int RPL>
+__device__ __forceinline__ unsigned every_epoch_slots(unsigned long long* shadow, unsigned long long n_words,
+                                                      unsigned act, const unsigned* idx, const unsigned* report_word,
+                                                      const unsigned* tid, const unsigned* op, unsigned bc,
+                                                      unsigned wc, unsigned kernel, const hr_geom& g,
+                                                      hr_region_dev* region, unsigned cap)
 {
-    return hr_ep_apply(shadow, n_words, idx, abs_word, tid, op, bc, wc, kern, g, region->ring, region->ring_cap,
-                       &region->n_races, &region->flags, region->region, cap);
+    const unsigned ktag = kernel & 7u;
+    unsigned err = 0;
+    auto holds = [&](int k) { return op[k] == HR_R ? 1u : (op[k] == HR_A ? 2u : 3u); };
+    auto against = [&](int k) { return op[k] == HR_R ? 2u : (op[k] == HR_A ? 1u : 3u); };
+    // 1. the held kinds' summaries, all loaded at once, then every first CAS
+    unsigned long long o[RPL][2], seen[RPL][2];
+    unsigned casm = 0;  // bit 2k+b: a CAS went out on summary b of slot k
+#pragma unroll
+    for (int k = 0; k < RPL; ++k)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (((act >> k) & 1u) && ((holds(k) >> b) & 1u)) o[k][b] = hr_ld_relaxed(shadow + b * n_words + idx[k]);
+#pragma unroll
+    for (int k = 0; k < RPL; ++k)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (!((act >> k) & 1u) || !((holds(k) >> b) & 1u)) continue;
+            const unsigned long long n = hr_ep_update(o[k][b], tid[k], bc, wc, ktag, g);
+            if (n == o[k][b]) continue;
+            seen[k][b] = atomicCAS(shadow + b * n_words + idx[k], o[k][b], n);
+            casm |= 1u << (2 * k + b);
+        }
+    // a CAS that lost: fold again into what it saw
+#pragma unroll
+    for (int k = 0; k < RPL; ++k)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            if (!((casm >> (2 * k + b)) & 1u) || seen[k][b] == o[k][b]) continue;
+            unsigned long long* p = shadow + b * n_words + idx[k];
+            unsigned long long cur = seen[k][b];
+            bool ok = false;
+            for (unsigned tries = 1; tries < cap; ++tries) {
+                const unsigned long long n = hr_ep_update(cur, tid[k], bc, wc, ktag, g);
+                if (n == cur) { ok = true; break; }
+                const unsigned long long sv = atomicCAS(p, cur, n);
+                if (sv == cur) { ok = true; break; }
+                cur = sv;
+            }
+            if (!ok) {
+                err = HR_ERR_CONTENTION;
+                act &= ~(1u << k);  // this access is not applied: it reports nothing
+            }
+        }
+    if (!act) return err;
+    asm volatile("fence.sc.gpu;" ::: "memory");
+    // 2. the conflicting kinds' summaries, all loaded at once
+    unsigned long long sv[RPL][2];
+#pragma unroll
+    for (int k = 0; k < RPL; ++k)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (((act >> k) & 1u) && ((against(k) >> b) & 1u)) sv[k][b] = hr_ld_relaxed(shadow + b * n_words + idx[k]);
+    // 3. a conflicting holder: claim the (kernel, epoch) of the report
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+        if (!((act >> k) & 1u)) continue;
+        unsigned prior = 0;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (!prior && ((against(k) >> b) & 1u) && hr_ep_pred(sv[k][b], tid[k], bc, wc, ktag, g))
+                prior = hr_ep_level(sv[k][b], ktag);
+        if (!prior) continue;
+        unsigned long long* st = shadow + 2 * n_words + idx[k];
+        const unsigned long long mine = ((((unsigned long long)kernel) << 16) | bc) + 1ull;
+        unsigned long long cur = hr_ld_relaxed(st);
+        bool claimed = false;
+        for (unsigned tries = 0; cur < mine && tries < cap; ++tries) {
+            const unsigned long long x = atomicCAS(st, cur, mine);
+            if (x == cur) { claimed = true; break; }
+            cur = x;
+        }
+        if (claimed)
+            hr_append_race(region->ring, region->ring_cap, &region->n_races, &region->flags, report_word[k], tid[k],
+                           kernel, bc, region->region, op[k], prior);
+        else if (cur < mine)
+            err = HR_ERR_CONTENTION;
+    }
+    return err;
 }
 
 template <int TILE>
@@ -1061,16 +1146,18 @@ __global__ void __launch_bounds__(Shape<HR_RPL, HR_CONSUMERS>::THREADS, Shape<HR
 
             if (every) {
                 if (!ready && !wait_dep(t_dep, t_need)) break;
+                unsigned ix[HR_RPL], rw[HR_RPL], tv[HR_RPL], ov[HR_RPL];
 #pragma unroll
                 for (int k = 0; k < HR_RPL; ++k) {
-                    if (!((actm >> k) & 1u)) continue;
                     const Acc me = my_acc[k * 32 + lane];
-                    const unsigned wd = my_word[k * 32 + lane];
-                    const unsigned abs_word = wd + (filtering ? (unsigned)filt.word_lo : 0u);
-                    const unsigned st = every_epoch_record(shadow, n_words, wd, abs_word, me.tid, me.op, bc, wc,
-                                                           kern, g, region, w.cas_cap);
-                    if (st) hr_set_error(&region->error, st);
+                    ix[k] = my_word[k * 32 + lane];
+                    rw[k] = ix[k] + (filtering ? (unsigned)filt.word_lo : 0u);
+                    tv[k] = me.tid;
+                    ov[k] = me.op;
                 }
+                const unsigned st = every_epoch_slots<HR_RPL>(shadow, n_words, actm, ix, rw, tv, ov, bc, wc, kern, g,
+                                                              region, w.cas_cap);
+                if (st) hr_set_error(&region->error, st);
             } else {
                 const bool spec = !ready;
                 if (!ready && !wait_dep(t_dep, t_need)) break;
