@@ -136,3 +136,25 @@ def test_mode_validation(hr):
         hr.Checker([dict(n_words=64, block_dim=32, report_mode=hr.REPORT_EVERY_EPOCH, shadow_bytes=4)])
     with pytest.raises(hr.HiRaceError):
         hr.Checker([dict(n_words=64, block_dim=32, report_mode=2)])
+
+
+def test_cas_retry_cap_reports_contention(hr):
+    """Every-epoch mode with zero retries allowed: 64K threads of 256 blocks
+    writing one word in one wave make some summary CAS lose, and the region
+    reports HR_ERR_CONTENTION; with the default cap the same trace gives the
+    one racy (word, kernel, epoch)."""
+    n = 1 << 16
+    tr = np.zeros(n, tg.RECORD)
+    tr["tid"] = np.arange(n)
+    tr["op"] = tg.OP_W
+    reg = dict(n_words=1, block_dim=256, report_mode=hr.REPORT_EVERY_EPOCH)
+    with hr.Checker([reg]) as ck:
+        ck.set_limits(cas_retry_cap=0)
+        ck.check_trace(0, to_dev(tr))
+        _, status, _, _ = ck.report(0)
+        assert hr.STATUS[status] == "HR_ERR_CONTENTION"
+        ck.set_limits()
+        ck.reset(0)
+        ck.check_trace(0, to_dev(tr))
+        races, status, n_total, _ = ck.report(0)
+        assert status == hr.HR_OK and n_total == 1
