@@ -28,13 +28,15 @@
 //                         shared-memory histogram, then writes the histogram
 //                         into the table column of that part
 //   2. hr_bin_scan_sums : the sum of each block of the table; the per-wave
-//                         shadow-clear flags; the "binned" flag
+//                         shadow-clear flags; the "binned" flag; the accesses
+//                         of the check and of its fullest segment, for the
+//                         skew guard (hr_bin_taken)
 //   3. hr_bin_scan      : exclusive scan of the table (segment-major, parts in
 //                         trace order) into bucket offsets
 //   4. hr_bin_scatter   : clusters of CTAs walk the same slices wave by wave;
-//                         each access, packed to 8 bytes (tid, op, word within
-//                         the segment), goes to its bucket's next slot (cursors
-//                         in distributed shared memory: no global atomics)
+//                         each access, packed to 4 or 8 bytes (tid, op, word
+//                         within the segment), goes to its bucket's next slot
+//                         (cursors in distributed shared memory: no global atomics)
 //   5. hr_bin_groups    : persistent thread groups, one segment at a time: its
 //                         shadow in shared memory (or zeros when nothing in it
 //                         is live), its accesses in wave order with a
@@ -358,19 +360,41 @@ __global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan_sums(hr_work w)
             w.ctl->bin_tbits = (w.ctl->fresh && fits) ? tb : 0u;
         }
     }
-    const unsigned long long E = (unsigned long long)w.bin.n_seg * w.ctl->bin_parts;
+    const unsigned P = w.ctl->bin_parts, n_seg = w.bin.n_seg;
+    const unsigned long long E = (unsigned long long)n_seg * P;
     const unsigned long long b0 = (unsigned long long)blockIdx.x * HR_BIN_SCAN;
     if (b0 >= E) return;
     unsigned v = 0;
     for (unsigned long long i = b0 + threadIdx.x; i < min(E, b0 + HR_BIN_SCAN); i += blockDim.x) v += w.bin.table[i];
     v = block_sum(v, s_warp);
-    if (threadIdx.x == 0) w.bin.sums[blockIdx.x] = v;
+    // the skew guard's inputs: the segments whose first entry lies in this block,
+    // each summed whole by one warp (its row may run into the next block)
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long s_lo = (b0 + P - 1) / P;
+    const unsigned long long s_hi = min((unsigned long long)n_seg, (min(E, b0 + HR_BIN_SCAN) + P - 1) / P);
+    unsigned m = 0;
+    for (unsigned long long sg = s_lo + wid; sg < s_hi; sg += blockDim.x >> 5) {
+        unsigned t = 0;
+        for (unsigned i = lane; i < P; i += 32) t += w.bin.table[sg * P + i];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        m = max(m, t);
+    }
+    __shared__ unsigned s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    if (lane == 0 && m) atomicMax(&s_max, m);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // one global atomic of each kind per block
+        w.bin.sums[blockIdx.x] = v;
+        if (v) atomicAdd(&w.ctl->bin_count, v);
+        if (s_max) atomicMax(&w.ctl->bin_max_seg, s_max);
+    }
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan(hr_work w)
 {
     __shared__ unsigned s_warp[32];
-    if (!w.ctl->binned) return;
+    if (!hr_bin_taken(w.ctl)) return;
     const unsigned long long E = (unsigned long long)w.bin.n_seg * w.ctl->bin_parts;
     const unsigned long long b0 = (unsigned long long)blockIdx.x * HR_BIN_SCAN;
     if (b0 >= E) return;
@@ -427,7 +451,7 @@ __global__ void __cluster_dims__(HR_BIN_CLUSTER, 1, 1) __launch_bounds__(STREAM_
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem& S = *reinterpret_cast<ScatterSmem*>(smem_raw);
     cg::cluster_group cluster = cg::this_cluster();
-    if (!w.ctl->binned) return;  // the same for every CTA: no remote access happens
+    if (!hr_bin_taken(w.ctl)) return;  // the same for every CTA: no remote access happens
     const unsigned W = w.ctl->n_waves, P = w.ctl->bin_parts;
     const hr_jobd jb = w.jobs[0];
     hr_region_dev* rg = regions + jb.region;
@@ -856,7 +880,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PCommon& C = *reinterpret_cast<PCommon*>(smem_raw);
     unsigned char* gbase = smem_raw + sizeof(PCommon);
-    if (!w.ctl->binned) return;
+    if (!hr_bin_taken(w.ctl)) return;
     const hr_jobd jb = w.jobs[0];
     hr_region_dev* rg = regions + jb.region;
     if (*(volatile unsigned*)&rg->error) return;

@@ -105,6 +105,9 @@ struct hr_stage {
     unsigned last;        // 1: the job's last stage (its completion time is recorded)
 };
 
+constexpr unsigned HR_BIN_SKEW = 256;           // a segment with more than 1/this of the accesses ...
+constexpr unsigned HR_BIN_SKEW_MIN = 1u << 22;  // ... of a check this large goes to the per-wave checker
+
 struct hr_ctl {
     unsigned ticket;       // next work item
     unsigned abort;        // set when a bounded wait expired
@@ -125,7 +128,19 @@ struct hr_ctl {
     unsigned bin_tbits;    // binned checker: 0, or the tid width of a 4-byte working shadow in shared memory
                            // (fresh checks whose tids and clocks fit it)
     unsigned seg_ticket;   // binned checker: next segment a thread group of the segment pass takes
+    unsigned bin_max_seg;  // binned checker: accesses of the fullest segment
+    unsigned bin_count;    // binned checker: accesses counted into buckets
 };
+
+// Whether the binned checker applies this check (the flag, and the skew guard:
+// one thread group applies a segment's accesses, so a large check whose fullest
+// segment holds more than 1/HR_BIN_SKEW of them - the hub words of a power-law
+// graph - goes to the per-wave checker instead, which is launched after the
+// binned kernels).  Read by the kernels after the count and scan passes.
+__host__ __device__ inline bool hr_bin_taken(const hr_ctl* c)
+{
+    return c->binned && !(c->bin_count >= HR_BIN_SKEW_MIN && (unsigned long long)c->bin_max_seg * HR_BIN_SKEW > c->bin_count);
+}
 
 // Scratch of the binned checker (hr_binned.cu), one per region.  The region's
 // shadow is cut into segments of HR_BIN_SEG words.  The trace is cut into one

@@ -186,6 +186,8 @@ __device__ void scan_counts_body(hr_work& w, unsigned total_int, hr_region_dev* 
         w.ctl->binned = 0;
         w.ctl->fresh = 0;
         w.ctl->bin_max_tid = 0;
+        w.ctl->bin_max_seg = 0;
+        w.ctl->bin_count = 0;
         w.ctl->n_waves = over ? 0u : (unsigned)total;
     }
 }
@@ -819,7 +821,7 @@ __device__ void producer_loop(hr_work& w, hr_region_dev* regions, uint4* s_rec, 
                               uint64_t* s_empty)
 {
     const uint64_t pol = policy_evict_first();
-    const unsigned total = w.ctl->binned ? 0u : w.ctl->total_items;  // binned: the work is done already
+    const unsigned total = hr_bin_taken(w.ctl) ? 0u : w.ctl->total_items;  // binned: the work is done already
     unsigned s = 0, s_begin = 0, s_end = 0, type = 0, dep = HR_NO_DEP, dep_need = 0, region = 0, last = 0;
     unsigned long long w_start = 0, w_end = 0, key = 0, kb = 0;
     const hr_record* trace = nullptr;

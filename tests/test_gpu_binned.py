@@ -178,6 +178,18 @@ def test_wide_tids_and_clocks(oracle_mod, hr):
     assert_parity(oracle_mod, hr, tr, SEG + 77, 64, 32, chunks=cuts)
 
 
+def test_skewed_large_check_falls_back(oracle_mod, hr):
+    """A check of at least 2^22 accesses whose largest segment holds more than
+    1/256 of them (here the hub words of a power-law graph: segment 0 holds
+    over a third) is handed to the per-wave checker by the skew guard; the
+    races are still the oracle's."""
+    tr, info = tg.gen_powerlaw_push(tg.seed_for(3, 22), log2_vertices=17, sweeps=2)
+    assert np.count_nonzero(tr["op"] <= 2) >= 1 << 22
+    seg0 = np.count_nonzero((tr["op"] <= 2) & (tr["word"] < 4096))
+    assert seg0 * 256 > len(tr)
+    assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"])
+
+
 def test_workloads(oracle_mod, hr):
     tr, info = tg.gen_global_mix(tg.seed_for(2, 21), inject=True, n_blocks=16)
     races, _ = assert_parity(oracle_mod, hr, tr, info["n_words"], info["block_dim"])
