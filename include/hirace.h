@@ -350,7 +350,10 @@ hr_status hr_destroy(hr_ctx* ctx);
  * wave) buckets and persistent thread groups apply each segment's buckets to a
  * shared-memory copy of the segment, wave by wave.  It takes single-trace checks of regions of at
  * most 2^26 words with at most 256 waves per call; batches, and calls it cannot
- * take, run the per-wave checker of id 3.  Its first check on a region
+ * take, run the per-wave checker of id 3.  So does a check of at least 2^22
+ * accesses whose fullest segment holds more than 1/256 of them (one thread
+ * group applies a segment, so a few hot words would serialise the check); that
+ * decision is taken on the device after the count and scan passes.  Its first check on a region
  * allocates the region's bucket tables (4 bytes per segment for each of 256
  * waves plus about one count slice per SM) and an access buffer of 8 bytes per
  * record, so make that check before capturing calls into a CUDA graph.  Its shared-memory CAS loops are bounded by the same cap.  hr_autotune checks the given trace on `region` with
