@@ -431,7 +431,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) hr_bin_scan(hr_work w)
 // rank s % HR_BIN_CLUSTER) and every CTA appends its share of the wave's
 // records with atomics on those cursors (distributed shared memory).  One
 // bucket range per cluster is being filled at a time, so L2 holds one partly
-// written sector per (cluster, segment) and merges the 8-byte stores.
+// written sector per (cluster, segment) and merges the 4- or 8-byte stores.
 
 constexpr unsigned CL = HR_BIN_CLUSTER;
 constexpr unsigned SCATTER_R = 4;  // records per thread per step: their atomics are in flight together
@@ -934,7 +934,7 @@ cudaError_t hr_launch_binned(hr_region_dev* d_regions, const hr_work& w, const u
                              cudaStream_t stream)
 {
     if (!g_attrs) {
-        // the shared-memory carveout at its maximum: 4 segment CTAs per SM
+        // the shared-memory carveout at its maximum (the groups kernel takes nearly all of it)
         for (const void* k : {(const void*)hr_bin_count, (const void*)hr_bin_groups<true>,
                               (const void*)hr_bin_groups<false>})
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

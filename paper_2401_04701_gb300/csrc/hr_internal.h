@@ -153,7 +153,7 @@ __host__ __device__ inline bool hr_bin_taken(const hr_ctl* c)
 #define HR_BIN_SEG_SHIFT_BITS 12
 #endif
 constexpr unsigned HR_BIN_SEG_SHIFT = HR_BIN_SEG_SHIFT_BITS;
-constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per segment (8 B each in shared memory)
+constexpr unsigned HR_BIN_SEG = 1u << HR_BIN_SEG_SHIFT;  // shadow words per segment (4 or 8 B each in shared memory)
 static_assert(HR_BIN_SEG_SHIFT >= 10 && HR_BIN_SEG_SHIFT <= 13, "the packed access keeps 16 bits for the word");
 constexpr unsigned HR_BIN_MAX_SEGS = 16384;              // larger regions take the per-wave checker
 constexpr unsigned HR_BIN_MAX_WAVES = 256;               // checks with more waves take the per-wave checker
