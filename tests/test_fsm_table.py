@@ -154,6 +154,7 @@ def _step_pow2(t, o, tid, op, bc, wc, ktag, bd_shift, ws_shift):
     return (hi << 32) | lo
 
 
+@pytest.mark.slow
 def test_an_applied_access_stays_absorbed(table):
     """Warp aggregation drops an access that repeats another lane's (same word,
     thread, op, wave), whatever else reaches the word in between.  That needs
